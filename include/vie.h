@@ -1,0 +1,246 @@
+/*
+ * vie.h - C ABI of libvie: the FFT-based volume-integral-equation (VIE)
+ * operator whose circulant Green's-function tensors are held Tucker
+ * (HOSVD) compressed, its adjoint, and the GMRES solve built on it.
+ *
+ * Method: Giannakopoulos, Litsarev, Polimeridis, "Memory footprint reduction
+ * for the FFT-based volume integral equation method via tensor
+ * decompositions".  Problem statement: the J-block of eqs. (1)-(4),
+ *     (M_eps_r - M_chi N) j = c_e M_chi e_inc ,
+ * with N of eq. (5) and the Green's function g of eq. (6).  Writing
+ * N = G + I, where G = (k0^2 + grad div) applied to the vector potential,
+ * and w = j / c_e, this is the library's system
+ *     A w = w - chi * (G w) = chi * e_inc .                        (S)
+ *
+ * Discretisation (uniform n1 x n2 x n3 grid of voxels of edge h, Section
+ * II.B): G is block-Toeplitz with Toeplitz blocks; its six unique dyadic
+ * components T_ab (ab = xx, xy, xz, yy, yz, zz) are the kernel
+ * (k0^2 delta_ab + d_a d_b) g sampled at voxel-centre offsets times h^3, and
+ * at zero offset the field of a uniform unit source in the equivalent
+ * sphere of radius a = h (3/4pi)^(1/3):
+ *     T_ab(0) = delta_ab [ (2/3)(1 + i k0 a) exp(-i k0 a) - 1 ].
+ * Each component is embedded in a circulant tensor of size
+ * P1 x P2 x P3 (P_q = 2 n_q; wrap-around planes at index n_q hold zero),
+ * DFT'd (Section V.A) and compressed by truncated HOSVD (Algorithm 1) to a
+ * core of size r1 x r2 x r3 and factors U^q (P_q x r_q), eqs. (13)-(14).
+ * The matvec (Section V.B) zero-pads and 3-D FFTs the current, rebuilds the
+ * components from core and factors, multiplies voxel by voxel, inverse-FFTs
+ * and crops.
+ *
+ * Conventions for every call:
+ *  - Arrays are C order, z fastest.  Vector fields are [B][3][n1][n2][n3]
+ *    (component a = x, y, z), scalar fields [n1][n2][n3].
+ *  - Complex numbers are interleaved (re, im): "c64" = 2 x float,
+ *    "c128" = 2 x double.  `precision` selects VIE_C64 or VIE_C128 for the
+ *    array arguments of a call.
+ *  - Pointers marked "device" must be CUDA device (or managed) memory owned
+ *    by the caller; the library never frees them.  Pointers marked "host"
+ *    are ordinary host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it unless stated otherwise.
+ *  - Every call returns a vie_status; a non-zero status leaves outputs
+ *    unspecified and is never signalled by abort().  vie_last_error()
+ *    returns a message for the last failure on the calling thread.
+ *  - Scratch memory is owned by the vie_op and grows on demand; call
+ *    vie_reserve() first if later calls must not allocate (for example
+ *    inside CUDA graph capture).
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vie_status {
+    VIE_OK = 0,
+    VIE_ERR_ARG = 1,             /* invalid argument or unsupported size      */
+    VIE_ERR_CUDA = 2,            /* a CUDA runtime call or launch failed      */
+    VIE_ERR_OOM = 3,             /* device or host allocation failed          */
+    VIE_ERR_NO_CONVERGENCE = 4,  /* solver hit its iteration limits           */
+    VIE_ERR_NUMERIC = 5,         /* NaN/Inf, breakdown or eigen-solver failure */
+    VIE_ERR_TIMEOUT = 6          /* a bounded device wait ran out             */
+} vie_status;
+
+enum { VIE_C64 = 0, VIE_C128 = 1 };                 /* array precision          */
+enum { VIE_PATH_TUCKER = 0, VIE_PATH_UNCOMPRESSED = 1 };
+
+/* HOSVD truncation rule (Algorithm 1; the printed rule is garbled):
+ * TAIL      - smallest r_q with sqrt(sum_{j>r_q} sigma_j^2) <= (tol/sqrt3)||A||_F,
+ *             which bounds ||A - A~||_F <= tol ||A||_F (eq. (12));
+ * SIGMA_MAX - keep sigma_j >= (tol/sqrt3) sigma_max.                           */
+enum { VIE_RANK_TAIL = 0, VIE_RANK_SIGMA_MAX = 1 };
+
+/* vie_tucker_compress flags */
+enum {
+    VIE_STORE_UNCOMPRESSED = 1,  /* also keep the six full spectra (the paper's
+                                    "traditional FFT-JVIE", Table II row 1) in
+                                    c64 and c128, for VIE_PATH_UNCOMPRESSED     */
+    VIE_SELF_TERM_PV = 2         /* self term without the -1/3 depolarisation  */
+};
+
+/* vie_solve flags */
+enum {
+    VIE_SOLVE_ADJOINT = 1,       /* solve A^H w = b instead of A w = b          */
+    VIE_SOLVE_RHS_INCIDENT = 2,  /* `rhs` is e_inc and b = chi * e_inc; else
+                                    `rhs` is b itself                           */
+    VIE_SOLVE_X0 = 4             /* `w` holds the initial guess on entry        */
+};
+
+typedef struct vie_grid {
+    int n1, n2, n3;      /* voxels per axis (x, y, z), each >= 1             */
+    double h;            /* voxel edge, metres (> 0)                          */
+    double freq_hz;      /* frequency; k0 = 2 pi f / c with c = 299792458 m/s */
+} vie_grid;
+
+typedef struct vie_op vie_op;    /* opaque; owns the device core/factors */
+
+typedef struct vie_op_info_t {
+    int n[3];                    /* grid                                       */
+    int P[3];                    /* padded (circulant) sizes 2 n_q              */
+    int ranks[6][3];             /* multilinear ranks per component (xx..zz)   */
+    size_t tucker_bytes;         /* c64 cores + factors as stored (half rows)   */
+    size_t tucker_bytes_full;    /* c64 cores + full factors (P_q rows), eq. (13)*/
+    size_t uncompressed_bytes;   /* six c64 spectra, 6 P1 P2 P3 x 8 bytes       */
+    size_t workspace_bytes;      /* scratch currently held                      */
+    int has_uncompressed;        /* VIE_STORE_UNCOMPRESSED was given            */
+    int max_batch;               /* batch size the scratch is sized for         */
+} vie_op_info_t;
+
+/* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */
+typedef struct vie_solve_opts {
+    double tol;          /* target FP64 relative residual ||b - A w||/||b||   */
+    int restart;         /* GMRES restart length m (1..128)                    */
+    int max_outer;       /* restart cycles allowed per inner solve            */
+    double inner_tol;    /* relative tolerance of each FP32 inner solve       */
+    int max_refine;      /* FP64 refinement steps allowed (<= 64)              */
+    int path;            /* VIE_PATH_TUCKER or VIE_PATH_UNCOMPRESSED            */
+    int use_graph;       /* replay each restart cycle as a CUDA graph         */
+    int refine;          /* 1: FP64 iterative refinement; 0: FP32 GMRES only  */
+} vie_solve_opts;
+
+typedef struct vie_solve_info {
+    int converged;           /* every RHS reached opts.tol                      */
+    int refine_steps;        /* FP64 residual evaluations after the first       */
+    int iterations;          /* inner Arnoldi iterations (all steps)            */
+    int matvecs;             /* operator applications (FP32 + FP64)             */
+    double relres;           /* final relative residual, max over RHS           */
+    double history[65];      /* relres after each refinement step               */
+} vie_solve_info;
+
+/*
+ * Build the compressed operator for `grid` (eqs. (5)-(6), Sections II.B and
+ * V.A, Algorithm 1): assemble each of the six defining tensors in FP64 on
+ * the device, embed it circulantly, 3-D FFT it, and compress it by
+ * truncated HOSVD at relative tolerance `tol` (> 0, < 1) with `rank_rule`.
+ * Cores and factors are kept in c64 (matvec) and c128 (refinement).
+ * Grid edges 2 n_q must factor into primes <= 7 and n_q <= 512.
+ * Synchronises `stream`.  On success *out receives a new operator that the
+ * caller releases with vie_destroy().
+ */
+int vie_tucker_compress(const vie_grid* grid, double tol, int rank_rule,
+                        int flags, void* stream, vie_op** out);
+
+/* Sizes, ranks and memory of `op` (host struct, filled on success). */
+int vie_op_info(const vie_op* op, vie_op_info_t* info);
+
+/*
+ * Copy component c (0..5 = xx, xy, xz, yy, yz, zz) of `op` to host buffers
+ * in c128: core [r1][r2][r3], factors U1 [P1][r1], U2 [P2][r2], U3 [P3][r3]
+ * (all P_q rows, so that eq. (13) rebuilds the full spectrum) and the
+ * singular values of the three unfoldings, sigma_q [P_q/2 + 1] each
+ * (descending; the unfolding has at most P_q/2 + 1 nonzero ones).  Any
+ * pointer may be NULL.  Synchronises `stream`.
+ */
+int vie_op_export(const vie_op* op, int c, double* core, double* U1, double* U2,
+                  double* U3, double* sigma1, double* sigma2, double* sigma3,
+                  void* stream);
+
+/*
+ * The uncompressed FFT'd circulant component c (Section V.A) for `grid`,
+ * c128 [P1][P2][P3] written to device memory `out`.  The first two steps of
+ * vie_tucker_compress, exposed for checking.
+ */
+int vie_green_spectrum(const vie_grid* grid, int c, int flags, void* out,
+                       void* stream);
+
+/* Size the scratch of `op` for batches of up to max_batch vectors, in
+ * both precisions.  Synchronous. */
+int vie_reserve(vie_op* op, int max_batch);
+
+/*
+ * Y = G J for B >= 1 vector fields (Section V.B): zero-pad, 3-D FFT, voxel-
+ * wise product with the six components (rebuilt from the Tucker form, eq.
+ * (13), or read from the stored spectra for VIE_PATH_UNCOMPRESSED), inverse
+ * FFT, crop.  J, Y: device [B][3][n1][n2][n3] in `precision`; Y may alias J.
+ */
+int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
+               int precision, void* stream);
+
+/* X = G^H Y = conj(G conj(Y)) (G is complex symmetric).  Layout as vie_matvec. */
+int vie_matvec_adjoint(const vie_op* op, const void* Y, void* X, int B,
+                       int path, int precision, void* stream);
+
+/*
+ * out = A w = w - chi * (G w)        (adjoint = 0), or
+ * out = A^H w = w - G^H (conj(chi) w) (adjoint = 1),  the operator of (S).
+ * chi: device [n1][n2][n3]; w, out: device [B][3][n1][n2][n3]; out may not
+ * alias w.
+ */
+int vie_apply_system(const vie_op* op, const void* chi, const void* w, void* out,
+                     int B, int adjoint, int path, int precision, void* stream);
+
+/* E = e_inc + G w, the total field of (S).  All device [B][3][n1][n2][n3]. */
+int vie_total_field(const vie_op* op, const void* einc, const void* w, void* E,
+                    int B, int path, int precision, void* stream);
+
+/*
+ * Solve (S) or its adjoint for B right-hand sides with GMRES (Section VI.C)
+ * in FP32 (c64 Krylov vectors, FP64 dot products, Hessenberg and Givens
+ * rotations), wrapped in FP64 iterative refinement when opts->refine:
+ * r = b - A w is formed with the FP64 operator and corrected by inner FP32
+ * solves until ||r||/||b|| <= opts->tol for every RHS.
+ * chi: device [n1][n2][n3]; rhs: device [B][3][n1][n2][n3] (e_inc or b per
+ * `flags`); w: device, same layout, receives the solution (and holds x0
+ * with VIE_SOLVE_X0).  Synchronises `stream` once per restart cycle.
+ * Returns VIE_ERR_NO_CONVERGENCE (with `info` filled) if the limits are hit.
+ */
+int vie_solve(const vie_op* op, const void* chi, const void* rhs, void* w, int B,
+              int flags, int precision, const vie_solve_opts* opts,
+              vie_solve_info* info, void* stream);
+
+/*
+ * Contrast gradient from a forward field E and an adjoint solution lam:
+ *   grad[v] = scale * sum_b sum_a lam[b,a,v] conj(E[b,a,v]).
+ * For the misfit L = sum |E - E_target|^2 with A^H lam = G^H (E - E_target)
+ * and scale = 2 this is dL/dRe chi + i dL/dIm chi (A dw = dchi E, dE = G dw).
+ * lam, E: device [B][3][n1][n2][n3]; grad: device [n1][n2][n3].
+ */
+int vie_contrast_gradient(const vie_op* op, const void* lam, const void* E,
+                          void* grad, int B, double scale, int precision,
+                          void* stream);
+
+/*
+ * Incident fields of B unit z-directed point dipoles at host points
+ * `sources` [B][3] (metres, box centre at the origin, voxel centres at
+ * (i + 1/2 - n/2) h): e_a(r) = (k0^2 delta_az + d_a d_z) g(r - r_s).
+ * out: device [B][3][n1][n2][n3].  A source at a voxel centre is an error.
+ */
+int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* out,
+                        int precision, void* stream);
+
+/* Release `op` and everything it owns (NULL is allowed). */
+void vie_destroy(vie_op* op);
+
+/* Static description of a status code. */
+const char* vie_status_string(int status);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIE_H */

@@ -57,6 +57,12 @@ def gradient(Ghat, chi, einc, E_target, tol=1e-12, restart=50, max_outer=400):
     return misfit(E, E_target), grad, finfo, ainfo
 
 
+def contrast_gradient(lam, E, scale=2.0):
+    """scale * sum over RHS and components of lam * conj(E) (per voxel)."""
+    g = scale * np.sum(lam * np.conj(E), axis=-4)
+    return g.sum(axis=0) if g.ndim == 4 else g
+
+
 def loss_of_chi(Ghat, chi, einc, E_target, tol=1e-12):
     _, E, _ = forward(Ghat, chi, einc, tol)
     return misfit(E, E_target)

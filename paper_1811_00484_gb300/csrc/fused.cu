@@ -1,0 +1,274 @@
+// Fused z-axis FFT, Tucker rebuild, voxel-wise product and inverse z-FFT:
+// the element-wise product of the matvec (Section V.B, Table II) done with
+// the components decompressed on chip instead of into a buffer.
+//
+// The rebuild follows eq. (13) in two stages:
+//   slab cores   S_c[k1] = core_c x1 U1_c[k1, :]            (r2 x r3)
+//   one fibre    G_c[k1, k2, k3] = sum_g ( U2_c[k2, :] S_c[k1] )[g] U3_c[k3, g]
+// The spectrum of every component is even or odd along each axis
+// (G_c[P - k] = s G_c[k], s = -1 when the component is odd in that
+// coordinate), and so are the HOSVD factors of its unfoldings.  One CTA
+// therefore rebuilds the fibre of (k1, k2) once, for k3 <= P3/2, and uses it,
+// with signs, for the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2) of every
+// right-hand side.  The stored (uncompressed) variant reads the six spectra
+// from memory instead.
+#include "fft.cuh"
+
+namespace vie {
+
+// sign of component c (xx, xy, xz, yy, yz, zz) under k_q -> P_q - k_q
+__constant__ int kParity[6][3] = {
+    {1, 1, 1}, {-1, -1, 1}, {-1, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, 1, 1}};
+
+template <typename T> struct SlabArgs {
+  const cx<T>* core[6];
+  const cx<T>* U1[6];
+  int r1[6], r2[6], r3[6];
+  cx<T>* slab;
+  long long slab_stride;
+  int r2max, r3max;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) slab_core_kernel(const SlabArgs<T> a) {
+  using C = cx<T>;
+  const int k1 = blockIdx.x, c = blockIdx.y;
+  const int r1 = a.r1[c], r2 = a.r2[c], r3 = a.r3[c];
+  const C* core = a.core[c];
+  const C* u1 = a.U1[c] + (long long)k1 * r1;
+  C* S = a.slab + c * a.slab_stride + (long long)k1 * a.r2max * a.r3max;
+  for (int it = threadIdx.x; it < r2 * r3; it += blockDim.x) {
+    const int b = it / r3, g = it % r3;
+    C acc = czero<C>();
+    for (int al = 0; al < r1; ++al) acc = cmadd(u1[al], core[(al * r2 + b) * r3 + g], acc);
+    S[b * a.r3max + g] = acc;
+  }
+}
+
+template <typename T> struct FusedArgs {
+  cx<T>* data;                 // [B*3][P1][P2][n3], transformed in place
+  const cx<T>* roots;          // P3-th roots of unity
+  FftPlan plan;
+  int n3, P1, P2, P3, H1, H2, H3;
+  int B;
+  long long comp_stride;       // P1 * P2 * n3
+  const CompMeta<T>* meta;     // [6] (Tucker)
+  int r2max, r3max;
+  const cx<T>* spec;           // [6][P1][P2][P3] (stored)
+  long long spec_stride;       // P1 * P2 * P3
+  const int* active;           // per RHS, nullptr = all
+  int lines_per_round;         // z-lines (x3 components) held in shared memory at once
+  int ld;                      // shared-memory line stride
+};
+
+template <typename T, bool STORED>
+__global__ void __launch_bounds__(256) fused_z_kernel(const FusedArgs<T> a) {
+  using C = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int P3 = a.P3, n3 = a.n3, ld = a.ld, H3 = a.H3;
+  const int g = blockIdx.x;
+  const int k1 = g / a.H2, k2 = g % a.H2;
+  const int xs0 = k1, xs1 = a.P1 - k1;
+  const int ys0 = k2, ys1 = a.P2 - k2;
+  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
+  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
+  const int nl = nx * ny;
+  const int LR = a.lines_per_round;
+
+  C* roots = reinterpret_cast<C*>(smem_raw);
+  C* ghalf = roots + P3;               // [6][H3]
+  C* wv = ghalf + 6 * H3;              // [6][r3max]
+  C* buf0 = wv + 6 * a.r3max;          // [LR*3][ld]
+  C* buf1 = buf0 + LR * 3 * ld;
+
+  for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
+
+  if (!STORED) {
+    for (int it = tid; it < 6 * a.r3max; it += nth) {
+      const int c = it / a.r3max, gm = it % a.r3max;
+      const CompMeta<T> m = a.meta[c];
+      C acc = czero<C>();
+      if (gm < m.r3) {
+        const C* S = m.slab + (long long)k1 * a.r2max * a.r3max;
+        const C* u2 = m.U2 + (long long)k2 * m.r2;
+        for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max + gm], acc);
+      }
+      wv[it] = acc;
+    }
+    __syncthreads();
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it % H3;
+      const CompMeta<T> m = a.meta[c];
+      const C* u3 = m.U3 + (long long)kk * m.r3;
+      const C* w = wv + c * a.r3max;
+      C acc = czero<C>();
+      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
+      ghalf[it] = acc;
+    }
+  }
+  __syncthreads();
+
+  for (int b = 0; b < a.B; ++b) {
+    if (a.active != nullptr && a.active[b] == 0) continue;   // block-uniform
+    for (int l0 = 0; l0 < nl; l0 += LR) {
+      const int nlr = min(LR, nl - l0);
+      const int nlines = nlr * 3;
+      for (int e = tid; e < nlines * P3; e += nth) {
+        const int line = e / P3, p = e % P3;
+        const int l = l0 + line / 3, comp = line % 3;
+        const int kx = (l / ny) ? xs1 : xs0, ky = (l % ny) ? ys1 : ys0;
+        C v = czero<C>();
+        if (p < n3)
+          v = a.data[(long long)(b * 3 + comp) * a.comp_stride + ((long long)kx * a.P2 + ky) * n3 + p];
+        buf0[line * ld + p] = v;
+      }
+      __syncthreads();
+      C* F = fft_lines<T, false>(buf0, buf1, a.plan, nlines, ld, 1, roots, false, tid, nth);
+      C* Fo = (F == buf0) ? buf1 : buf0;
+
+      for (int e = tid; e < nlr * P3; e += nth) {
+        const int lr = e / P3, kk = e % P3;
+        const int l = l0 + lr;
+        const int ix = l / ny, iy = l % ny;
+        C* base = F + lr * 3 * ld + kk;
+        const C jx = base[0], jy = base[ld], jz = base[2 * ld];
+        C gc[6];
+        if (STORED) {
+          const int kx = ix ? xs1 : xs0, ky = iy ? ys1 : ys0;
+          const long long off = ((long long)kx * a.P2 + ky) * P3 + kk;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) gc[c] = a.spec[c * a.spec_stride + off];
+        } else {
+          const bool zm = 2 * kk > P3;
+          const int fold = zm ? P3 - kk : kk;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            int s = 1;
+            if (ix) s *= kParity[c][0];
+            if (iy) s *= kParity[c][1];
+            if (zm) s *= kParity[c][2];
+            const C v = ghalf[c * H3 + fold];
+            gc[c] = (s > 0) ? v : mk(-v.x, -v.y);
+          }
+        }
+        // Y_a = sum_b G_ab J_b with G symmetric: xx xy xz / xy yy yz / xz yz zz
+        base[0] = gc[0] * jx + gc[1] * jy + gc[2] * jz;
+        base[ld] = gc[1] * jx + gc[3] * jy + gc[4] * jz;
+        base[2 * ld] = gc[2] * jx + gc[4] * jy + gc[5] * jz;
+      }
+      __syncthreads();
+      C* R = fft_lines<T, false>(F, Fo, a.plan, nlines, ld, 1, roots, true, tid, nth);
+
+      for (int e = tid; e < nlines * n3; e += nth) {
+        const int line = e / n3, p = e % n3;
+        const int l = l0 + line / 3, comp = line % 3;
+        const int kx = (l / ny) ? xs1 : xs0, ky = (l % ny) ? ys1 : ys0;
+        a.data[(long long)(b * 3 + comp) * a.comp_stride + ((long long)kx * a.P2 + ky) * n3 + p] =
+            R[line * ld + p];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+static size_t fused_smem(const FusedArgs<T>& a, int LR) {
+  return (size_t)(a.P3 + 6 * a.H3 + 6 * a.r3max + 2 * LR * 3 * a.ld) * sizeof(cx<T>);
+}
+
+template <typename T, bool STORED>
+static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
+  const size_t limit = 227 * 1024;
+  int LR = 4;
+  while (LR > 1 && fused_smem(a, LR) > limit) LR /= 2;
+  if (fused_smem(a, LR) > limit) {
+    set_error("fused kernel: line length %d needs more shared memory than available", a.P3);
+    return VIE_ERR_ARG;
+  }
+  a.lines_per_round = LR;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(fused_z_kernel<T, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)limit);
+    attr_done = true;
+  }
+  fused_z_kernel<T, STORED><<<a.H1 * a.H2, 256, fused_smem(a, LR), s>>>(a);
+  return VIE_OK;
+}
+
+}  // namespace vie
+
+// ---------------------------------------------------------------------------
+// host launchers used by matvec.cu
+// ---------------------------------------------------------------------------
+template <typename T>
+int launch_slab_cores(const vie_op* op, cudaStream_t s) {
+  vie::SlabArgs<T> a;
+  for (int c = 0; c < 6; ++c) {
+    const TuckerComp& tc = op->comp[c];
+    if constexpr (sizeof(T) == 4) {
+      a.core[c] = tc.core32;
+      a.U1[c] = tc.U32[0];
+    } else {
+      a.core[c] = tc.core64;
+      a.U1[c] = tc.U64[0];
+    }
+    a.r1[c] = tc.r[0];
+    a.r2[c] = tc.r[1];
+    a.r3[c] = tc.r[2];
+  }
+  if constexpr (sizeof(T) == 4) a.slab = op->slab32; else a.slab = op->slab64;
+  a.slab_stride = (long long)op->slab_stride;
+  a.r2max = op->rmax[1];
+  a.r3max = op->rmax[2];
+  dim3 grid(op->H[0], 6);
+  vie::slab_core_kernel<T><<<grid, 256, 0, s>>>(a);
+  return VIE_OK;
+}
+
+template <typename T>
+int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
+                 cudaStream_t s) {
+  vie::FusedArgs<T> a;
+  a.data = data;
+  if constexpr (sizeof(T) == 4) {
+    a.roots = op->roots32[2];
+    a.spec = op->spec32;
+    a.meta = reinterpret_cast<const CompMeta<T>*>(op->meta);
+  } else {
+    a.roots = op->roots64[2];
+    a.spec = op->spec64;
+    a.meta = reinterpret_cast<const CompMeta<T>*>(static_cast<char*>(op->meta) +
+                                                  6 * sizeof(CompMeta<float>));
+  }
+  a.plan = op->plan[2];
+  a.n3 = op->n[2];
+  a.P1 = op->P[0];
+  a.P2 = op->P[1];
+  a.P3 = op->P[2];
+  a.H1 = op->H[0];
+  a.H2 = op->H[1];
+  a.H3 = op->H[2];
+  a.B = B;
+  a.comp_stride = (long long)op->P[0] * op->P[1] * op->n[2];
+  a.r2max = op->rmax[1];
+  a.r3max = op->rmax[2];
+  a.spec_stride = (long long)op->P[0] * op->P[1] * op->P[2];
+  a.active = active;
+  a.ld = op->P[2];
+  a.lines_per_round = 4;
+  if (stored) {
+    if (a.spec == nullptr) {
+      set_error("operator was built without VIE_STORE_UNCOMPRESSED");
+      return VIE_ERR_ARG;
+    }
+    return vie::launch_fused_impl<T, true>(a, s);
+  }
+  return vie::launch_fused_impl<T, false>(a, s);
+}
+
+template int launch_slab_cores<float>(const vie_op*, cudaStream_t);
+template int launch_slab_cores<double>(const vie_op*, cudaStream_t);
+template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t);
+template int launch_fused<double>(const vie_op*, double2*, int, bool, const int*, cudaStream_t);

@@ -1,0 +1,121 @@
+// Strided line FFTs: the x- and y-axis stages of the zero-padded forward
+// FFT and of the cropped inverse FFT of the matvec (Section V.B), and the
+// full 3-D FFT of the FP64 spectrum assembly (Section V.A).
+//
+// One CTA transforms TW lines that sit next to each other in memory (a tile
+// of TW consecutive columns), so that every global load and store of a
+// line position is a contiguous run of TW complex numbers.  Zero padding
+// (points lin..N-1 read as zero), cropping (only points < lout stored),
+// conjugation, the contrast product and the final scale/subtract of the
+// system operator are fused into the load and store loops.
+#include "fft.cuh"
+
+namespace vie {
+
+template <typename T, int TW>
+__global__ void __launch_bounds__(256) line_fft_kernel(const LineArgs<T> a) {
+  using C = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.plan.N;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);   // element (col c, pos p) at p*TW + c
+  C* buf1 = buf0 + N * TW;
+  C* roots = buf1 + N * TW;
+
+  const int c0 = blockIdx.x * TW;
+  const int o = blockIdx.y;
+  const int bb = blockIdx.z;
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ncols = min(TW, a.ncol - c0);
+
+  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0 * a.in_cs;
+  const bool col_fast_in = (a.in_cs == 1);
+  for (int e = tid; e < N * TW; e += nth) {
+    int p, c;
+    if (col_fast_in) { c = e % TW; p = e / TW; } else { p = e % N; c = e / N; }
+    C v = czero<C>();
+    if (p < a.lin && c < ncols) {
+      v = in[p * a.in_ls + c * a.in_cs];
+      if (a.flags & PRO_CONJ) v = conjg(v);
+      if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c) * a.chi_cs] * v;
+    }
+    buf0[p * TW + c] = v;
+  }
+  __syncthreads();
+
+  C* res = fft_lines<T, true>(buf0, buf1, a.plan, TW, 1, TW, roots, a.inverse != 0, tid, nth);
+
+  const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0 * a.out_cs;
+  C* out = a.out + obase;
+  const bool col_fast_out = (a.out_cs == 1);
+  for (int e = tid; e < a.lout * TW; e += nth) {
+    int p, c;
+    if (col_fast_out) { c = e % TW; p = e / TW; } else { p = e % a.lout; c = e / a.lout; }
+    if (c >= ncols) continue;
+    C v = a.scale * res[p * TW + c];
+    if (a.flags & EPI_CONJ) v = conjg(v);
+    const long long oi = p * a.out_ls + c * a.out_cs;
+    if (a.flags & (EPI_SUB | EPI_ADD)) {
+      if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c) * a.chi_cs] * v;
+      const C w = a.addend[obase + oi];
+      v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
+    }
+    out[oi] = v;
+  }
+}
+
+template <typename T, int TW>
+static void launch_tw(const LineArgs<T>& a, size_t smem, cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(line_fft_kernel<T, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr_done = true;
+  }
+  dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
+  line_fft_kernel<T, TW><<<grid, 256, smem, s>>>(a);
+}
+
+// Widest tile (16, 8 or 4 lines; 128 bytes per row for c64 at 16) whose two
+// ping-pong buffers and root table fit in 227 KB of shared memory.
+template <typename T>
+void launch_line_fft(const LineArgs<T>& a, cudaStream_t s) {
+  const int N = a.plan.N;
+  auto bytes = [&](int tw) { return (size_t)(2 * N * tw + N) * sizeof(cx<T>); };
+  const size_t limit = 227 * 1024;
+  if constexpr (sizeof(T) == 4) {
+    if (bytes(16) <= limit) {
+      launch_tw<T, 16>(a, bytes(16), s);
+      return;
+    }
+  }
+  if (bytes(8) <= limit) launch_tw<T, 8>(a, bytes(8), s);
+  else launch_tw<T, 4>(a, bytes(4), s);
+}
+
+}  // namespace vie
+
+template <typename T>
+void launch_line_fft(const LineArgs<T>& a, cudaStream_t s) {
+  vie::launch_line_fft<T>(a, s);
+}
+template void launch_line_fft<float>(const LineArgs<float>&, cudaStream_t);
+template void launch_line_fft<double>(const LineArgs<double>&, cudaStream_t);
+
+bool make_plan(int N, FftPlan* plan) {
+  plan->N = N;
+  plan->npass = 0;
+  if (N < 1 || N > VIE_MAX_N) return false;
+  int m = N;
+  static const int order[] = {8, 4, 2, 3, 5, 7};
+  for (int r : order) {
+    while (m % r == 0) {
+      if (plan->npass == VIE_MAX_PASSES) return false;
+      plan->radix[plan->npass++] = r;
+      m /= r;
+    }
+  }
+  return m == 1;
+}

@@ -1,0 +1,165 @@
+// Host orchestration of the FFT-based matvec (Section V.B):
+//
+//   J [B][3][n1][n2][n3]
+//     -- x-FFT, zero-padded n1 -> P1 -->            T1 [B][3][P1][n2][n3]
+//     -- y-FFT, zero-padded n2 -> P2 -->            T2 [B][3][P1][P2][n3]
+//     -- fused: z-FFT n3 -> P3, rebuild + product,
+//        inverse z-FFT cropped P3 -> n3 -->         T2 (in place)
+//     -- inverse y-FFT, cropped P2 -> n2 -->        T1
+//     -- inverse x-FFT, cropped P1 -> n1, scaled
+//        by 1/(P1 P2 P3), optional epilogue -->    Y [B][3][n1][n2][n3]
+//
+// Lines that are entirely zero padding are never transformed: the x stage
+// runs n2 n3 lines, the y stage P1 n3 lines.
+#include "vie_internal.cuh"
+
+template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
+template <typename T>
+int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
+                 cudaStream_t s);
+
+size_t workspace_bytes_for(const vie_op* op, int B) {
+  const size_t n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
+  const size_t P1 = op->P[0], P2 = op->P[1];
+  const size_t per = 3 * (P1 * n2 * n3 + P1 * P2 * n3);   // T1 + T2 elements per RHS
+  return per * (size_t)B * sizeof(double2);                // sized for the FP64 path
+}
+
+int ensure_workspace(vie_op* op, int B) {
+  const size_t need = workspace_bytes_for(op, B);
+  if (op->ws.bytes >= need) return VIE_OK;
+  if (op->ws.ptr) {
+    cudaDeviceSynchronize();
+    cudaFree(op->ws.ptr);
+    op->ws.ptr = nullptr;
+    op->ws.bytes = 0;
+    op->ws_batch = 0;
+  }
+  cudaError_t e = cudaMalloc(&op->ws.ptr, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("workspace allocation of %zu bytes failed", need);
+    return VIE_ERR_OOM;
+  }
+  op->ws.bytes = need;
+  op->ws_batch = B;
+  return VIE_OK;
+}
+
+template <typename T>
+int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
+                int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
+                cudaStream_t s) {
+  using C = cx<T>;
+  if (workspace_bytes_for(op, B) > op->ws.bytes) {
+    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
+  }
+  const bool stored = (path == VIE_PATH_UNCOMPRESSED);
+  const long long n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
+  const long long P1 = op->P[0], P2 = op->P[1], P3 = op->P[2];
+  C* T1 = static_cast<C*>(op->ws.ptr);
+  C* T2 = T1 + (size_t)B * 3 * P1 * n2 * n3;
+  const C* r[3];
+  for (int q = 0; q < 3; ++q) {
+    if constexpr (sizeof(T) == 4) r[q] = op->roots32[q]; else r[q] = op->roots64[q];
+  }
+
+  if (!stored) VIE_TRY(launch_slab_cores<T>(op, s));
+
+  // x stage: J -> T1
+  {
+    LineArgs<T> a = {};
+    a.in = in;
+    a.out = T1;
+    a.roots = r[0];
+    a.chi = chi;
+    a.plan = op->plan[0];
+    a.lin = (int)n1;
+    a.lout = (int)P1;
+    a.inverse = 0;
+    a.scale = (T)1;
+    a.flags = pro_flags & (PRO_CONJ | PRO_CHI);
+    a.nbatch = 3 * B;
+    a.nother = (int)n2;
+    a.ncol = (int)n3;
+    a.in_bs = n1 * n2 * n3; a.in_os = n3; a.in_ls = n2 * n3; a.in_cs = 1;
+    a.out_bs = P1 * n2 * n3; a.out_os = n3; a.out_ls = n2 * n3; a.out_cs = 1;
+    a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
+    a.batch_per_rhs = 3;
+    a.active = active;
+    launch_line_fft<T>(a, s);
+  }
+  // y stage: T1 -> T2
+  {
+    LineArgs<T> a = {};
+    a.in = T1;
+    a.out = T2;
+    a.roots = r[1];
+    a.plan = op->plan[1];
+    a.lin = (int)n2;
+    a.lout = (int)P2;
+    a.scale = (T)1;
+    a.nbatch = 3 * B;
+    a.nother = (int)P1;
+    a.ncol = (int)n3;
+    a.in_bs = P1 * n2 * n3; a.in_os = n2 * n3; a.in_ls = n3; a.in_cs = 1;
+    a.out_bs = P1 * P2 * n3; a.out_os = P2 * n3; a.out_ls = n3; a.out_cs = 1;
+    a.batch_per_rhs = 3;
+    a.active = active;
+    launch_line_fft<T>(a, s);
+  }
+  // z stage fused with the rebuild and the product
+  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s));
+  // inverse y stage: T2 -> T1 (crop)
+  {
+    LineArgs<T> a = {};
+    a.in = T2;
+    a.out = T1;
+    a.roots = r[1];
+    a.plan = op->plan[1];
+    a.lin = (int)P2;
+    a.lout = (int)n2;
+    a.inverse = 1;
+    a.scale = (T)1;
+    a.nbatch = 3 * B;
+    a.nother = (int)P1;
+    a.ncol = (int)n3;
+    a.in_bs = P1 * P2 * n3; a.in_os = P2 * n3; a.in_ls = n3; a.in_cs = 1;
+    a.out_bs = P1 * n2 * n3; a.out_os = n2 * n3; a.out_ls = n3; a.out_cs = 1;
+    a.batch_per_rhs = 3;
+    a.active = active;
+    launch_line_fft<T>(a, s);
+  }
+  // inverse x stage: T1 -> out (crop, scale, epilogue)
+  {
+    LineArgs<T> a = {};
+    a.in = T1;
+    a.out = out;
+    a.roots = r[0];
+    a.chi = chi;
+    a.addend = addend;
+    a.plan = op->plan[0];
+    a.lin = (int)P1;
+    a.lout = (int)n1;
+    a.inverse = 1;
+    a.scale = (T)(1.0 / ((double)P1 * (double)P2 * (double)P3));
+    a.flags = epi_flags & (EPI_CONJ | EPI_SUB | EPI_ADD | EPI_CHI);
+    a.nbatch = 3 * B;
+    a.nother = (int)n2;
+    a.ncol = (int)n3;
+    a.in_bs = P1 * n2 * n3; a.in_os = n3; a.in_ls = n2 * n3; a.in_cs = 1;
+    a.out_bs = n1 * n2 * n3; a.out_os = n3; a.out_ls = n2 * n3; a.out_cs = 1;
+    a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
+    a.batch_per_rhs = 3;
+    a.active = active;
+    launch_line_fft<T>(a, s);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "matvec launch");
+  return VIE_OK;
+}
+
+template int matvec_impl<float>(const vie_op*, const float2*, float2*, int, int, int, int,
+                                const float2*, const float2*, const int*, cudaStream_t);
+template int matvec_impl<double>(const vie_op*, const double2*, double2*, int, int, int, int,
+                                 const double2*, const double2*, const int*, cudaStream_t);

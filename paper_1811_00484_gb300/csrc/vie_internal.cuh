@@ -1,0 +1,187 @@
+// Internal declarations of libvie (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "vie.h"
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cx = typename cplx<T>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+#define VIE_CX_OPS(C, T)                                                                  \
+  __host__ __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); } \
+  __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
+  __host__ __device__ __forceinline__ C operator*(C a, C b) {                               \
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                                 \
+  }                                                                                         \
+  __host__ __device__ __forceinline__ C operator*(T s, C a) { return mk(s * a.x, s * a.y); } \
+  __host__ __device__ __forceinline__ C conjg(C a) { return mk(a.x, -a.y); }                \
+  __host__ __device__ __forceinline__ C mul_i(C a) { return mk(-a.y, a.x); }               \
+  __host__ __device__ __forceinline__ C mul_mi(C a) { return mk(a.y, -a.x); }              \
+  __host__ __device__ __forceinline__ C cmadd(C a, C b, C c) { /* a*b + c */               \
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));      \
+  }                                                                                         \
+  __host__ __device__ __forceinline__ C conj_madd(C a, C b, C c) { /* conj(a)*b + c */     \
+    return mk(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));      \
+  }                                                                                         \
+  __host__ __device__ __forceinline__ T abs2(C a) { return a.x * a.x + a.y * a.y; }
+VIE_CX_OPS(float2, float)
+VIE_CX_OPS(double2, double)
+#undef VIE_CX_OPS
+
+template <typename C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// ---------------------------------------------------------------------------
+// FFT plan: mixed-radix Stockham, radices 8, 4, 2, 3, 5, 7.
+// ---------------------------------------------------------------------------
+#define VIE_MAX_PASSES 12
+#define VIE_MAX_N 1024
+struct FftPlan {
+  int N;
+  int npass;
+  int radix[VIE_MAX_PASSES];
+};
+bool make_plan(int N, FftPlan* plan);   // false if N has a prime factor > 7
+
+// ---------------------------------------------------------------------------
+// Line-FFT stage parameters (strided lines along one axis of a 3-D array).
+// Element (batch bb, other o, line position p, tile column c) lives at
+//   bb*bs + o*os + p*ls + c*cs   (separately for input and output).
+// ---------------------------------------------------------------------------
+enum {
+  PRO_CONJ = 1,      // conjugate the input
+  PRO_CHI = 2,       // multiply the input by chi[p, o, c] (scalar field)
+  EPI_CONJ = 4,      // conjugate the (scaled) result
+  EPI_SUB = 8,       // out = addend - (chi?) result
+  EPI_ADD = 16,      // out = addend + result
+  EPI_CHI = 32       // multiply the result by chi before EPI_SUB
+};
+
+template <typename T> struct LineArgs {
+  const cx<T>* in;
+  cx<T>* out;
+  const cx<T>* roots;      // N-th roots of unity exp(-2 pi i m / N), m < N
+  const cx<T>* chi;        // scalar field (PRO_CHI / EPI_CHI)
+  const cx<T>* addend;     // EPI_SUB / EPI_ADD, laid out like `out`
+  FftPlan plan;
+  int lin, lout;           // points loaded (rest zero) / points stored
+  int inverse;
+  T scale;
+  int flags;
+  int nbatch, nother, ncol;            // grid extents
+  long long in_bs, in_os, in_ls, in_cs;
+  long long out_bs, out_os, out_ls, out_cs;
+  long long chi_os, chi_ls, chi_cs;    // chi index = o*chi_os + p*chi_ls + c*chi_cs
+  int batch_per_rhs;                   // batches per RHS (3 components) for `active`
+  const int* active;                   // per-RHS flag (nullptr = all active)
+};
+
+template <typename T> void launch_line_fft(const LineArgs<T>& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Operator state
+// ---------------------------------------------------------------------------
+struct TuckerComp {
+  int r[3];            // multilinear ranks
+  int s[3];            // parity sign of the spectrum along each axis
+  float2* core32 = nullptr;  double2* core64 = nullptr;   // [r1][r2][r3]
+  float2* U32[3] = {};       double2* U64[3] = {};        // half factors [H_q][r_q]
+  std::vector<double> sigma[3];                            // H_q singular values
+};
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct vie_op {
+  vie_grid grid;
+  int n[3], P[3], H[3];
+  double k0;
+  int flags;
+  TuckerComp comp[6];
+  int rmax[3];
+  // slab cores S_c[k1] = core_c x1 U1_c[k1, :], rebuilt at every matvec
+  float2* slab32 = nullptr;  double2* slab64 = nullptr;
+  size_t slab_stride;        // elements per component: H1 * rmax2 * rmax3
+  // stored spectra (optional)
+  float2* spec32 = nullptr;  double2* spec64 = nullptr;
+  FftPlan plan[3];
+  float2* roots32[3] = {};   double2* roots64[3] = {};
+  // device copy of per-component metadata for the fused kernel
+  void* meta = nullptr;
+  Workspace ws;
+  int ws_batch = 0;
+  // solver scratch
+  Workspace solve_ws;
+  void* solver = nullptr;    // cached solver state (graphs), see solve.cu
+};
+
+// Per-component data read by the fused kernel (device copy in op->meta).
+template <typename T> struct CompMeta {
+  const cx<T>* U2;   // [H2][r2]
+  const cx<T>* U3;   // [H3][r3]
+  const cx<T>* slab; // [H1][r2][r3] (row stride rmax)
+  int r2, r3;
+  int s1, s2, s3;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+int cuda_status(cudaError_t e, const char* what);
+#define VIE_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return cuda_status(e__, #call);     \
+  } while (0)
+#define VIE_TRY(call)                        \
+  do {                                       \
+    int st__ = (call);                       \
+    if (st__ != VIE_OK) return st__;         \
+  } while (0)
+
+int check_grid(const vie_grid* g);
+int component_parity(int c, int axis);     // +1 / -1
+void component_axes(int c, int* a, int* b);
+double wavenumber(double freq_hz);
+
+// matvec internals (matvec.cu)
+template <typename T>
+int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
+                int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
+                cudaStream_t s);
+int ensure_workspace(vie_op* op, int B);
+size_t workspace_bytes_for(const vie_op* op, int B);
+
+// setup internals (setup.cu)
+int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,
+                   vie_op** out);
+int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s);
+int op_tables(vie_op* op);   // FFT plans and root tables of op->P
+
+// solver (solve.cu)
+int solve_impl(const vie_op* op, const void* chi, const void* rhs, void* w, int B, int flags,
+               int precision, const vie_solve_opts* opts, vie_solve_info* info, cudaStream_t s);
+void solver_release(vie_op* op);
+
+// elementwise kernels (blas.cu)
+template <typename T>
+int launch_gradient(const cx<T>* lam, const cx<T>* E, cx<T>* grad, int B, double scale,
+                    long long nvox, cudaStream_t s);
+template <typename T>
+int launch_dipole(const vie_op* op, const double* src_dev, int B, cx<T>* out, cudaStream_t s);

@@ -1,0 +1,66 @@
+"""The C ABI: libvie loads, exports every symbol include/vie.h declares, and
+rejects bad arguments on the host (no GPU needed for these paths)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "vie.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vie_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(vie.lib, name), name
+    assert sorted(vie.EXPORTS) == declared
+
+
+def test_status_strings():
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    for code, text in vie.STATUS.items():
+        assert vie.lib.vie_status_string(code).decode() == text
+    assert vie.lib.vie_status_string(99).decode() == "unknown status"
+
+
+@pytest.mark.parametrize("grid,tol,msg", [
+    ((0, 4, 4, 5e-3, 3e8), 1e-6, "outside"),
+    ((4, 4, 513, 5e-3, 3e8), 1e-6, "outside"),
+    ((11, 4, 4, 5e-3, 3e8), 1e-6, "prime factor"),      # 22 = 2 * 11
+    ((4, 4, 4, -1.0, 3e8), 1e-6, "voxel edge"),
+    ((4, 4, 4, 5e-3, 3e8), 0.0, "tol"),
+    ((4, 4, 4, 5e-3, 3e8), 1.5, "tol"),
+])
+def test_compress_rejects_bad_arguments_before_any_cuda_call(grid, tol, msg):
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    g = vie.Grid(*grid)
+    h = ctypes.c_void_p()
+    st = vie.lib.vie_tucker_compress(ctypes.byref(g), tol, 0, 0, None, ctypes.byref(h))
+    assert st == 1
+    assert msg in vie.lib.vie_last_error().decode()
+    assert not h.value
+
+
+def test_null_operator_is_rejected():
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    info = vie.OpInfo()
+    assert vie.lib.vie_op_info(None, ctypes.byref(info)) == 1
+    assert vie.lib.vie_matvec(None, None, None, 1, 0, 0, None) == 1
+    assert vie.lib.vie_solve(None, None, None, None, 1, 0, 0, None, None, None) == 1
+    vie.lib.vie_destroy(None)
+
+
+def test_struct_layouts_match_header():
+    """ctypes mirrors of the header structs have the C sizes."""
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    assert ctypes.sizeof(vie.Grid) == 3 * 4 + 4 + 2 * 8
+    assert ctypes.sizeof(vie.SolveOpts) == 8 + 4 + 4 + 8 + 4 * 4
+    assert ctypes.sizeof(vie.SolveInfo) == 4 * 4 + 8 + 65 * 8

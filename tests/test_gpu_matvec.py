@@ -1,0 +1,234 @@
+"""GPU parity of the setup and of the matvec against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 paths (c128): the same arithmetic up to rounding order, <= 1e-11
+    relative L2 (measured ~1e-14; FFT rounding grows like log N).
+  * FP32 paths (c64): the matvec gate of 1e-5 relative L2.  FP32 FFTs and
+    the FP32 rebuild contribute ~ few x 6e-8 x log2(P) per stage.
+  * The Tucker operator is compared with the oracle's own HOSVD of the same
+    spectra; ranks must agree unless a singular value lies within 1e-9 of
+    the truncation threshold (then either rank is correct).
+Grids include non-cubic and ragged shapes (line tiles of 16 with a tail,
+radix-3/5/7 FFT lengths) and the 16^3 matvec workload.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import adjoint as AD
+from oracle import embed as E
+from oracle import hosvd as H
+from oracle import kernel as K
+from oracle import matvec as M
+
+vie = pytest.importorskip("paper_1811_00484_gb300")
+pytestmark = pytest.mark.gpu
+
+F = 298e6
+HVOX = 5e-3
+K0 = K.wavenumber(F)
+
+GRIDS = [(3, 4, 5), (8, 8, 8), (6, 10, 20), (7, 5, 12), (16, 16, 16), (20, 9, 35)]
+
+
+def dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+_cache = {}
+
+
+def setup_case(n, tol=1e-8, rule="tail", store=True):
+    key = (n, tol, rule, store)
+    if key not in _cache:
+        n1, n2, n3 = n
+        T = K.toeplitz_tensor(n1, n2, n3, HVOX, K0)
+        Ghat = E.green_spectra(T, n1, n2, n3)
+        comp = H.compress_components(Ghat, tol, rule)
+        op = vie.Operator(n, HVOX, F, tol, rank_rule=rule, store_uncompressed=store)
+        _cache[key] = (T, Ghat, comp, H.rebuild_components(comp), op)
+    return _cache[key]
+
+
+def rand_field(n, B=1, seed=0):
+    rng = np.random.default_rng(seed)
+    shape = (B, 3) + tuple(n)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("n", GRIDS[:4])
+def test_green_spectrum_matches_oracle(n):
+    n1, n2, n3 = n
+    Ghat = E.green_spectra(K.toeplitz_tensor(n1, n2, n3, HVOX, K0), n1, n2, n3)
+    for c in range(6):
+        g = host(vie.green_spectrum(n, HVOX, F, c))
+        assert rel(g, Ghat[c]) <= 1e-12, c
+
+
+@pytest.mark.parametrize("n,tol,rule", [((8, 8, 8), 1e-8, "tail"), ((16, 16, 16), 1e-8, "tail"),
+                                        ((16, 16, 16), 1e-4, "sigma_max"), ((6, 10, 20), 1e-6, "tail"),
+                                        ((20, 9, 35), 1e-6, "tail")])
+def test_hosvd_singular_values_ranks_and_reconstruction(n, tol, rule):
+    T, Ghat, comp, rebuilt, op = setup_case(n, tol, rule)
+    ranks = op.info()["ranks"]
+    for c in range(6):
+        core, U, S = op.export(c)
+        _, Uo, So = comp[c]
+        smax = So[0][0]
+        for q in range(3):
+            h = n[q] + 1
+            s_ref = So[q][:h] if So[q].size >= h else np.pad(So[q], (0, h - So[q].size))
+            assert np.max(np.abs(S[q] - s_ref)) <= 1e-11 * smax, (c, q)
+            # the sigma-max rule compares singular values; the tail rule their tails
+            if ranks[c][q] != Uo[q].shape[1]:
+                thr = tol / math.sqrt(3) * (smax if rule == "sigma_max" else np.linalg.norm(Ghat[c]))
+                r = min(ranks[c][q], Uo[q].shape[1])
+                if rule == "sigma_max":
+                    near = abs(So[q][r] - thr) <= 1e-9 * smax
+                else:
+                    near = abs(math.sqrt(np.sum(So[q][r:] ** 2)) - thr) <= 1e-9 * smax
+                assert near, (c, q, ranks[c][q], Uo[q].shape[1])
+            assert np.allclose(U[q].conj().T @ U[q], np.eye(U[q].shape[1]), atol=1e-12)
+        At = H.tucker_full(core, U)
+        nrm = np.linalg.norm(Ghat[c])
+        assert np.linalg.norm(At - Ghat[c]) <= tol * nrm * (1 + 1e-9) + 1e-13 * nrm, c
+        if tuple(core.shape) == tuple(u.shape[1] for u in Uo):
+            assert np.linalg.norm(At - rebuilt[c]) <= 1e-10 * nrm, c
+
+
+@pytest.mark.parametrize("n", GRIDS)
+def test_matvec_fp32_and_fp64_tucker(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    J = rand_field(n, B=2, seed=1)
+    ref = M.matvec_fft(rebuilt, J)
+    y32 = host(op.matvec(dev(J)))
+    y64 = host(op.matvec(dev(J, torch.complex128)))
+    assert rel(y32, ref) <= 1e-5
+    assert rel(y64, ref) <= 1e-11
+    exact = M.matvec_fft(Ghat, J)
+    assert rel(y64, exact) <= 1e-8 * 4          # HOSVD truncation at 1e-8
+
+
+@pytest.mark.parametrize("n", [(3, 4, 5), (6, 10, 20), (16, 16, 16)])
+def test_matvec_uncompressed_paths(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    J = rand_field(n, B=1, seed=2)
+    exact = M.matvec_fft(Ghat, J)
+    assert rel(host(op.matvec(dev(J), path="uncompressed")), exact) <= 1e-5
+    assert rel(host(op.matvec(dev(J, torch.complex128), path="uncompressed")), exact) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [(3, 4, 5), (7, 5, 12)])
+def test_matvec_equals_bruteforce_toeplitz_sum(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    J = rand_field(n, B=1, seed=3)
+    bf = M.matvec_bruteforce(T, J)
+    assert rel(host(op.matvec(dev(J, torch.complex128), path="uncompressed")), bf) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [(6, 10, 20), (16, 16, 16)])
+def test_adjoint_matvec_and_identity(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    x = rand_field(n, seed=4)
+    y = rand_field(n, seed=5)
+    ref = AD.adjoint_matvec(rebuilt, y)
+    assert rel(host(op.matvec_adjoint(dev(y))), ref) <= 1e-5
+    a64 = host(op.matvec_adjoint(dev(y, torch.complex128)))
+    assert rel(a64, ref) <= 1e-11
+    gx = host(op.matvec(dev(x, torch.complex128)))
+    lhs = np.vdot(gx, y)
+    rhs = np.vdot(x, a64)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("n", [(6, 10, 20), (16, 16, 16)])
+def test_system_operator_and_total_field(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    wl = workloads.make("t", n, seed=6, incident="plane")
+    w = rand_field(n, seed=7)
+    chi = wl.chi
+    ref = M.apply_system(rebuilt, chi, w)
+    refh = AD.apply_system_adjoint(rebuilt, chi, w)
+    for dt, tol_ in ((torch.complex64, 1e-5), (torch.complex128, 1e-11)):
+        assert rel(host(op.apply_system(dev(chi, dt), dev(w, dt))), ref) <= tol_
+        assert rel(host(op.apply_system(dev(chi, dt), dev(w, dt), adjoint=True)), refh) <= tol_
+        Et = host(op.total_field(dev(wl.einc, dt), dev(w, dt)))
+        assert rel(Et, wl.einc + M.matvec_fft(rebuilt, w)) <= tol_
+
+
+def test_batch_rows_are_independent():
+    n = (6, 10, 20)
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    J = rand_field(n, B=3, seed=8)
+    yb = op.matvec(dev(J))
+    for b in range(3):
+        y1 = op.matvec(dev(J[b:b + 1]))
+        assert torch.equal(yb[b:b + 1], y1)
+
+
+def test_workload_n16_matvec_operator_and_adjoint():
+    """The 16^3 workload (tol 1e-8, seed 0): G J, A J and G^H J against the oracle."""
+    wl = workloads.matvec_n16()
+    n = wl.n
+    T, Ghat, comp, rebuilt, op = setup_case(n, wl.tol_svd)
+    J = wl.J
+    assert rel(host(op.matvec(dev(J))), M.matvec_fft(Ghat, J)) <= 1e-5
+    assert rel(host(op.apply_system(dev(wl.chi), dev(J))), M.apply_system(Ghat, wl.chi, J)) <= 1e-5
+    assert rel(host(op.matvec_adjoint(dev(J))), AD.adjoint_matvec(Ghat, J)) <= 1e-5
+
+
+def test_dipole_incident_field():
+    n = (6, 10, 20)
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    src = workloads.ring_dipoles(4)
+    ref = K.dipole_incident(*n, HVOX, K0, src)
+    assert rel(host(op.incident_dipole(src, dtype=torch.complex128)), ref) <= 1e-13
+    assert rel(host(op.incident_dipole(src)), ref) <= 1e-6
+    with pytest.raises(vie.VieError):
+        op.incident_dipole(np.array([[0.5 * HVOX, 0.5 * HVOX, 0.5 * HVOX]]))   # a voxel centre
+
+
+def test_contrast_gradient_kernel():
+    n = (6, 10, 20)
+    T, Ghat, comp, rebuilt, op = setup_case(n)
+    lam = rand_field(n, B=2, seed=9)
+    Ef = rand_field(n, B=2, seed=10)
+    ref = AD.contrast_gradient(lam, Ef, 2.0)
+    g = host(op.contrast_gradient(dev(lam, torch.complex128), dev(Ef, torch.complex128)))
+    assert rel(g, ref) <= 1e-14
+
+
+def test_uncompressed_path_requires_stored_spectra():
+    n = (3, 4, 5)
+    T, Ghat, comp, rebuilt, op = setup_case(n, store=False)
+    with pytest.raises(vie.VieError) as e:
+        op.matvec(dev(rand_field(n)), path="uncompressed")
+    assert e.value.status == 1
+
+
+def test_full_size_n64_matvec():
+    """The 64^3 solve workload at its bench launch shape (B = 1, FP32, Tucker at 1e-6)."""
+    wl = workloads.solve_n64()
+    n = wl.n
+    op = vie.Operator(n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=True)
+    J = wl.J
+    T = K.toeplitz_tensor(*n, wl.h, K0)
+    exact = M.matvec_fft(E.green_spectra(T, *n), J)
+    y_t = host(op.matvec(dev(J)))
+    y_u = host(op.matvec(dev(J), path="uncompressed"))
+    assert rel(y_u, exact) <= 1e-5
+    assert rel(y_t, exact) <= 1e-5 + 4 * wl.tol_svd
+    info = op.info()
+    assert info["tucker_bytes"] * 100 < info["uncompressed_bytes"]
+    op.close()
