@@ -187,12 +187,6 @@ static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
     return VIE_ERR_ARG;
   }
   a.lines_per_round = LR;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(fused_z_kernel<T, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)limit);
-    attr_done = true;
-  }
   fused_z_kernel<T, STORED><<<a.H1 * a.H2, 256, fused_smem(a, LR), s>>>(a);
   return VIE_OK;
 }
@@ -266,6 +260,16 @@ int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* a
     return vie::launch_fused_impl<T, true>(a, s);
   }
   return vie::launch_fused_impl<T, false>(a, s);
+}
+
+int fused_init_attributes() {
+  const int lim = 227 * 1024;
+  cudaError_t e = cudaSuccess;
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");
 }
 
 template int launch_slab_cores<float>(const vie_op*, cudaStream_t);

@@ -68,12 +68,6 @@ __global__ void __launch_bounds__(256) line_fft_kernel(const LineArgs<T> a) {
 
 template <typename T, int TW>
 static void launch_tw(const LineArgs<T>& a, size_t smem, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(line_fft_kernel<T, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_done = true;
-  }
   dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
   line_fft_kernel<T, TW><<<grid, 256, smem, s>>>(a);
 }
@@ -103,6 +97,19 @@ void launch_line_fft(const LineArgs<T>& a, cudaStream_t s) {
 }
 template void launch_line_fft<float>(const LineArgs<float>&, cudaStream_t);
 template void launch_line_fft<double>(const LineArgs<double>&, cudaStream_t);
+
+// Opt every line kernel into the full 227 KB of dynamic shared memory (once
+// per device, before any launch or graph capture).
+int line_fft_init_attributes() {
+  const int lim = 227 * 1024;
+  cudaError_t e = cudaSuccess;
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "line kernel attributes");
+}
 
 bool make_plan(int N, FftPlan* plan) {
   plan->N = N;

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* jobs, int
   __shared__ double cs[JACOBI_MAX_PAIRS];
   __shared__ double2 se[JACOBI_MAX_PAIRS];
   __shared__ int pp[JACOBI_MAX_PAIRS], qq[JACOBI_MAX_PAIRS];
+  __shared__ double dpp[JACOBI_MAX_PAIRS], dqq[JACOBI_MAX_PAIRS];
   __shared__ int rotated;
   const int tid = threadIdx.x, nth = blockDim.x;
   for (long long e = tid; e < (long long)m * m; e += nth)
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* jobs, int
         if (p > q) { int t = p; p = q; q = t; }
         double c = 1.0;
         double2 sv = make_double2(0.0, 0.0);
+        double np_ = 0.0, nq_ = 0.0;
         if (q < m) {
           const double app = A[(long long)p * m + p].x, aqq = A[(long long)q * m + q].x;
           const double2 apq = A[(long long)p * m + q];
@@ -235,10 +237,13 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* jobs, int
             c = 1.0 / sqrt(t * t + 1.0);
             const double s = t * c;
             sv = make_double2(s * apq.x / mag, s * apq.y / mag);   // s e^{i phi}
+            np_ = app - t * mag;                                    // rotated diagonal
+            nq_ = aqq + t * mag;
             rotated = 1;
           }
         }
         cs[i] = c; se[i] = sv; pp[i] = p; qq[i] = q < m ? q : -1;
+        dpp[i] = np_; dqq[i] = nq_;
       }
       __syncthreads();
       // A <- J^* A (rows p, q)
@@ -262,6 +267,18 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiJob* jobs, int
         const double2 vp = V[ip], vq = V[iq];
         V[ip] = cs[i] * vp - conjg(se[i]) * vq;
         V[iq] = se[i] * vp + cs[i] * vq;
+      }
+      __syncthreads();
+      // the rotation annihilates a_pq exactly and moves t|a_pq| between a_pp and a_qq;
+      // writing those values (instead of the rounded updates) lets the relative
+      // stopping test be met on graded matrices
+      for (int i = tid; i < npair; i += nth) {
+        if (qq[i] < 0 || (se[i].x == 0.0 && se[i].y == 0.0)) continue;
+        const long long p = pp[i], q = qq[i];
+        A[p * m + q] = make_double2(0.0, 0.0);
+        A[q * m + p] = make_double2(0.0, 0.0);
+        A[p * m + p] = make_double2(dpp[i], 0.0);
+        A[q * m + q] = make_double2(dqq[i], 0.0);
       }
       __syncthreads();
     }
@@ -365,6 +382,8 @@ int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s) {
 }
 
 static int init_tables(vie_op* op) {
+  VIE_TRY(line_fft_init_attributes());
+  VIE_TRY(fused_init_attributes());
   for (int q = 0; q < 3; ++q) {
     const int N = op->P[q];
     if (!make_plan(N, &op->plan[q])) {

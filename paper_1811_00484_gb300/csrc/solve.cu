@@ -1,10 +1,829 @@
-// GMRES solve with FP64 iterative refinement (Section VI.C).
+// GMRES solve of the J-block system (Section VI.C: restarted GMRES) with FP64
+// iterative refinement.
+//
+// Outer loop (FP64):  r = b - A x with the FP64 operator; stop when
+//   ||r_b|| / ||b_b|| <= tol for every right-hand side b; otherwise solve
+//   A d = r / ||r|| with FP32 GMRES and update x += ||r|| d.
+// Inner loop (FP32 vectors): restarted GMRES(m), B right-hand sides at once.
+//   Arnoldi by classical Gram-Schmidt applied twice (CGS2) with FP64 dot
+//   products, FP64 Hessenberg matrix and complex Givens rotations, FP64
+//   triangular solve.  Each restart cycle (m Arnoldi steps, the update of the
+//   iterate and the next cycle's true residual) is one CUDA graph: kernels
+//   read their state (active flags, iteration counts) from device memory,
+//   so converged right-hand sides drop out without host synchronisation;
+//   the host synchronises once per cycle.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "vie_internal.cuh"
 
-int solve_impl(const vie_op*, const void*, const void*, void*, int, int, int, const vie_solve_opts*,
-               vie_solve_info*, cudaStream_t) {
-  set_error("vie_solve is not available in this build");
-  return VIE_ERR_ARG;
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPer = 4;                       // elements per thread in the BLAS kernels
+constexpr int kChunk = kThreads * kPer;       // elements per CTA
+
+__device__ __forceinline__ double2 wsum(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
 }
 
-void solver_release(vie_op*) {}
+// partial[b][i][chunk] = sum over the chunk of conj(V_i[b]) w[b], i = 0..k
+__global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict__ V,
+                                                        const float2* __restrict__ w, int k, int B,
+                                                        long long N, int nchunk, double2* partial,
+                                                        const int* active) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (!active[b]) return;
+  __shared__ double2 red[kThreads / 32][129];
+  const long long base = (long long)chunk * kChunk;
+  float2 wv[kPer];
+#pragma unroll
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = base + e * kThreads + threadIdx.x;
+    wv[e] = idx < N ? w[(long long)b * N + idx] : make_float2(0.f, 0.f);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = 0; i <= k; ++i) {
+    const float2* vi = V + ((long long)i * B + b) * N;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const long long idx = base + e * kThreads + threadIdx.x;
+      if (idx < N) {
+        const float2 v = vi[idx];
+        acc.x += (double)v.x * wv[e].x + (double)v.y * wv[e].y;
+        acc.y += (double)v.x * wv[e].y - (double)v.y * wv[e].x;
+      }
+    }
+    acc = wsum(acc);
+    if (lane == 0) red[warp][i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= k; i += kThreads) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < kThreads / 32; ++q) s = s + red[q][i];
+    partial[((long long)b * 129 + i) * nchunk + chunk] = s;
+  }
+}
+
+// w[b] -= sum_i coef[b][i] V_i[b]; optionally partial norms of the result
+__global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restrict__ V, float2* w,
+                                                          const double2* coef, int k, int B,
+                                                          long long N, int nchunk, double* nrm_partial,
+                                                          const int* active) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (!active[b]) return;
+  __shared__ float2 c[129];
+  __shared__ double red[kThreads / 32];
+  for (int i = threadIdx.x; i <= k; i += kThreads) {
+    const double2 v = coef[(long long)b * 129 + i];
+    c[i] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const long long base = (long long)chunk * kChunk;
+  double nrm = 0.0;
+#pragma unroll
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = base + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      float2 acc = w[(long long)b * N + idx];
+      for (int i = 0; i <= k; ++i) {
+        const float2 v = V[((long long)i * B + b) * N + idx];
+        acc.x -= c[i].x * v.x - c[i].y * v.y;
+        acc.y -= c[i].x * v.y + c[i].y * v.x;
+      }
+      w[(long long)b * N + idx] = acc;
+      nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
+    }
+  }
+  if (nrm_partial) {
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) s += red[q];
+      nrm_partial[(long long)b * nchunk + chunk] = s;
+    }
+  }
+}
+
+// coef[b][i] = sum_chunk partial; H[b][k][i] += coef (column k of the Hessenberg matrix)
+__global__ void reduce_dots_kernel(const double2* partial, int k, int nchunk, double2* coef,
+                                   double2* H, int m, int accumulate, const int* active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i > k) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int c = lane; c < nchunk; c += 32) s = s + partial[((long long)b * 129 + i) * nchunk + c];
+  s = wsum(s);
+  if (lane == 0) {
+    coef[(long long)b * 129 + i] = s;
+    double2* h = H + ((long long)b * m + k) * (m + 1) + i;
+    *h = accumulate ? (*h + s) : s;
+  }
+}
+
+// out[b] = sqrt(sum_chunk partial[b][chunk])
+__global__ void reduce_norm_kernel(const double* partial, int nchunk, double* out, const int* active) {
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += 32) s += partial[(long long)b * nchunk + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[b] = sqrt(s);
+}
+
+// partial norms of an FP32 vector batch
+__global__ void __launch_bounds__(kThreads) norm32_kernel(const float2* v, long long N, int nchunk,
+                                                          double* partial, const int* active) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (active && !active[b]) return;
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)chunk * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const float2 x = v[(long long)b * N + idx];
+      s += (double)x.x * x.x + (double)x.y * x.y;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+    partial[(long long)b * nchunk + chunk] = t;
+  }
+}
+
+// One Givens step per RHS: finish column k (h_{k+1,k} = nrm), rotate, test convergence,
+// and store 1/h_{k+1,k} for the normalisation of the next basis vector.
+__global__ void givens_kernel(double2* H, double2* cs, double2* sn, double2* g, const double* nrm,
+                              double* inv, int k, int m, int B, int* active, int* iters,
+                              const double* tol_abs, int* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  count[b] += 1;
+  double2* h = H + ((long long)b * m + k) * (m + 1);
+  const double hk1 = nrm[b];
+  h[k + 1] = make_double2(hk1, 0.0);
+  double2* c = cs + (long long)b * m;
+  double2* s = sn + (long long)b * m;
+  for (int i = 0; i < k; ++i) {
+    const double2 t = c[i] * h[i] + s[i] * h[i + 1];
+    h[i + 1] = (-1.0) * (conjg(s[i]) * h[i]) + conjg(c[i]) * h[i + 1];
+    h[i] = t;
+  }
+  const double2 a = h[k], bb = h[k + 1];
+  const double den = sqrt(abs2(a) + abs2(bb));
+  double2 ck, sk;
+  if (den == 0.0) {
+    ck = make_double2(1.0, 0.0);
+    sk = make_double2(0.0, 0.0);
+  } else {
+    ck = (1.0 / den) * conjg(a);
+    sk = (1.0 / den) * conjg(bb);
+  }
+  c[k] = ck;
+  s[k] = sk;
+  h[k] = ck * a + sk * bb;
+  h[k + 1] = make_double2(0.0, 0.0);
+  double2* gb = g + (long long)b * (m + 1);
+  gb[k + 1] = (-1.0) * (conjg(sk) * gb[k]);
+  gb[k] = ck * gb[k];
+  iters[b] = k + 1;
+  const double res = sqrt(abs2(gb[k + 1]));
+  const bool breakdown = !(hk1 > 1e-300) || !(sqrt(abs2(h[k])) > 0.0);
+  if (res <= tol_abs[b] || breakdown || k + 1 == m || !(res == res)) active[b] = 0;
+  inv[b] = hk1 > 1e-300 ? 1.0 / hk1 : 0.0;
+}
+
+// V_{k+1}[b] = w[b] * inv[b]  (only for RHS still active after the Givens step)
+__global__ void __launch_bounds__(kThreads) scale_into_kernel(const float2* w, float2* dst,
+                                                              const double* inv, long long N,
+                                                              const int* active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const float s = (float)inv[b];
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)blockIdx.x * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const float2 v = w[(long long)b * N + idx];
+      dst[(long long)b * N + idx] = make_float2(s * v.x, s * v.y);
+    }
+  }
+}
+
+// y = R^-1 g over the iters[b] columns of the rotated Hessenberg matrix
+__global__ void backsolve_kernel(const double2* H, const double2* g, double2* y, int m, int B,
+                                 const int* iters) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int kk = iters[b];
+  const double2* gb = g + (long long)b * (m + 1);
+  double2* yb = y + (long long)b * 129;
+  for (int i = kk - 1; i >= 0; --i) {
+    double2 s = gb[i];
+    for (int j = i + 1; j < kk; ++j) s = s - H[((long long)b * m + j) * (m + 1) + i] * yb[j];
+    const double2 d = H[((long long)b * m + i) * (m + 1) + i];
+    const double dd = abs2(d);
+    yb[i] = dd > 0.0 ? (1.0 / dd) * (s * conjg(d)) : make_double2(0.0, 0.0);
+  }
+}
+
+// d[b] += sum_{j < iters[b]} y[b][j] V_j[b]
+__global__ void __launch_bounds__(kThreads) combine_kernel(const float2* V, float2* d, const double2* y,
+                                                           int B, long long N, const int* iters) {
+  const int b = blockIdx.y;
+  const int kk = iters[b];
+  if (kk == 0) return;
+  __shared__ float2 c[129];
+  for (int i = threadIdx.x; i < kk; i += kThreads) {
+    const double2 v = y[(long long)b * 129 + i];
+    c[i] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)blockIdx.x * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      float2 acc = d[(long long)b * N + idx];
+      for (int j = 0; j < kk; ++j) {
+        const float2 v = V[((long long)j * B + b) * N + idx];
+        acc.x += c[j].x * v.x - c[j].y * v.y;
+        acc.y += c[j].x * v.y + c[j].y * v.x;
+      }
+      d[(long long)b * N + idx] = acc;
+    }
+  }
+}
+
+// r = rhs - Ad (FP32), for RHS still to be solved; partial norms of r
+__global__ void __launch_bounds__(kThreads) residual32_kernel(const float2* rhs, const float2* ad,
+                                                              float2* r, long long N, int nchunk,
+                                                              double* partial, const int* want) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (!want[b]) return;
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)chunk * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const long long o = (long long)b * N + idx;
+      const float2 v = make_float2(rhs[o].x - ad[o].x, rhs[o].y - ad[o].y);
+      r[o] = v;
+      s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+    partial[(long long)b * nchunk + chunk] = t;
+  }
+}
+
+// start of a cycle: beta = ||r||, g = (beta, 0, ...), iters = 0, active = want && beta > tol
+__global__ void cycle_start_kernel(const double* beta, double2* g, double* inv, int m, int B,
+                                   const int* want, int* active, int* iters, const double* tol_abs,
+                                   int* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  iters[b] = 0;
+  if (count && want[b]) count[b] += 1;   // the residual matvec that produced beta
+  const bool go = want[b] && beta[b] > tol_abs[b] && beta[b] == beta[b];
+  active[b] = go ? 1 : 0;
+  double2* gb = g + (long long)b * (m + 1);
+  for (int i = 0; i <= m; ++i) gb[i] = make_double2(0.0, 0.0);
+  gb[0] = make_double2(go ? beta[b] : 0.0, 0.0);
+  inv[b] = go ? 1.0 / beta[b] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels of the refinement loop (templated on the I/O precision)
+// ---------------------------------------------------------------------------
+template <typename Tin>
+__global__ void load_rhs_kernel(const cx<Tin>* rhs, const cx<Tin>* chi, double2* b, long long nvox,
+                                int B, int incident) {
+  const long long total = 3LL * nvox * B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 v = make_double2((double)rhs[i].x, (double)rhs[i].y);
+    if (incident) {
+      const cx<Tin> c = chi[i % nvox];
+      v = make_double2((double)c.x, (double)c.y) * v;
+    }
+    b[i] = v;
+  }
+}
+
+template <typename Tout>
+__global__ void convert_kernel(const double2* x, cx<Tout>* out, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    cx<Tout> o;
+    o.x = (Tout)x[i].x;
+    o.y = (Tout)x[i].y;
+    out[i] = o;
+  }
+}
+
+template <typename Tin>
+__global__ void load_x_kernel(const cx<Tin>* in, double2* x, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+// r = b - Ax and partial ||r||^2, ||b||^2 (FP64)
+__global__ void __launch_bounds__(kThreads) residual64_kernel(const double2* b, const double2* ax,
+                                                              double2* r, long long N, int nchunk,
+                                                              double* pr, double* pb, int have_ax) {
+  const int rb = blockIdx.y, chunk = blockIdx.x;
+  __shared__ double red[2][kThreads / 32];
+  double sr = 0.0, sb = 0.0;
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)chunk * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const long long o = (long long)rb * N + idx;
+      const double2 bv = b[o];
+      const double2 v = have_ax ? bv - ax[o] : bv;
+      r[o] = v;
+      sr += abs2(v);
+      sb += abs2(bv);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) {
+      t0 += red[0][q];
+      t1 += red[1][q];
+    }
+    pr[(long long)rb * nchunk + chunk] = t0;
+    pb[(long long)rb * nchunk + chunk] = t1;
+  }
+}
+
+// r32 = r / scale (FP32), d = 0, for RHS that still need work
+__global__ void __launch_bounds__(kThreads) to_inner_kernel(const double2* r, const double* scale,
+                                                            float2* r32, float2* d, long long N,
+                                                            const int* want) {
+  const int b = blockIdx.y;
+  if (!want[b]) return;
+  const double s = scale[b] > 0.0 ? 1.0 / scale[b] : 0.0;
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)blockIdx.x * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const long long o = (long long)b * N + idx;
+      r32[o] = make_float2((float)(s * r[o].x), (float)(s * r[o].y));
+      d[o] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// x += scale * d  (FP64), for RHS that were worked on
+__global__ void __launch_bounds__(kThreads) accumulate_kernel(double2* x, const float2* d,
+                                                              const double* scale, long long N,
+                                                              const int* want) {
+  const int b = blockIdx.y;
+  if (!want[b]) return;
+  const double s = scale[b];
+  for (int e = 0; e < kPer; ++e) {
+    const long long idx = (long long)blockIdx.x * kChunk + e * kThreads + threadIdx.x;
+    if (idx < N) {
+      const long long o = (long long)b * N + idx;
+      x[o] = x[o] + make_double2(s * d[o].x, s * d[o].y);
+    }
+  }
+}
+
+__global__ void reduce_norm2_kernel(const double* partial, int nchunk, double* out, int B) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += 32) s += partial[(long long)b * nchunk + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[b] = sqrt(s);
+}
+
+int grid1(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(b, 152 * 16));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// solver state, cached on the operator
+// ---------------------------------------------------------------------------
+struct SolverState {
+  int B = 0, m = 0, path = -1;
+  long long N = 0;
+  int nchunk = 0;
+  size_t bytes = 0;
+  char* base = nullptr;
+  float2 *V, *W, *d, *r32;
+  double2 *H, *cs, *sn, *g, *coef, *partial;
+  double *nrm_partial, *nrm, *inv, *beta, *tol_abs, *rnorm, *bnorm, *pb;
+  int *active, *iters, *want, *count_it, *count_mv;
+  double2 *x, *b64, *r64, *ax64;
+  float2* chi32;
+  double2* chi64;
+  // graph of one restart cycle
+  // the solve runs on its own stream (graphs cannot be captured on the legacy
+  // default stream), ordered after and before the caller's stream by events
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* graph_chi = nullptr;
+  const void* graph_ws = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int graph_adjoint = -1;
+};
+
+static void release_state(SolverState* st) {
+  if (!st) return;
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->stream) {
+    cudaStreamSynchronize(st->stream);
+    cudaStreamDestroy(st->stream);
+  }
+  if (st->ev_in) cudaEventDestroy(st->ev_in);
+  if (st->ev_out) cudaEventDestroy(st->ev_out);
+  cudaFree(st->base);
+  delete st;
+}
+
+void solver_release(vie_op* op) {
+  release_state(static_cast<SolverState*>(op->solver));
+  op->solver = nullptr;
+}
+
+template <typename T> static T* carve(char*& p, size_t count) {
+  T* r = reinterpret_cast<T*>(p);
+  p += ((count * sizeof(T) + 255) / 256) * 256;
+  return r;
+}
+
+static size_t carve_bytes(int B, int m, long long N, int nchunk) {
+  char* p = nullptr;
+  carve<float2>(p, (size_t)(m + 1) * B * N);          // V
+  carve<float2>(p, (size_t)B * N);                    // W
+  carve<float2>(p, (size_t)B * N);                    // d
+  carve<float2>(p, (size_t)B * N);                    // r32
+  carve<double2>(p, (size_t)B * m * (m + 1));         // H
+  carve<double2>(p, (size_t)B * m);                   // cs
+  carve<double2>(p, (size_t)B * m);                   // sn
+  carve<double2>(p, (size_t)B * (m + 1));             // g
+  carve<double2>(p, (size_t)B * 129);                 // coef / y
+  carve<double2>(p, (size_t)B * 129 * nchunk);        // partial dots
+  carve<double>(p, (size_t)B * nchunk);               // norm partials
+  for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm inv beta tol_abs rnorm bnorm
+  carve<double>(p, (size_t)B * nchunk);               // pb
+  for (int i = 0; i < 5; ++i) carve<int>(p, B);       // active iters want counters
+  for (int i = 0; i < 4; ++i) carve<double2>(p, (size_t)B * N);   // x b64 r64 ax64
+  carve<float2>(p, (size_t)N / 3);                    // chi32
+  carve<double2>(p, (size_t)N / 3);                   // chi64
+  return (size_t)(p - (char*)nullptr);
+}
+
+static int get_state(vie_op* op, int B, int m, SolverState** out) {
+  SolverState* st = static_cast<SolverState*>(op->solver);
+  const long long N = 3LL * op->n[0] * op->n[1] * op->n[2];
+  if (st && st->B == B && st->m == m) {
+    *out = st;
+    return VIE_OK;
+  }
+  release_state(st);
+  op->solver = nullptr;
+  op->solve_ws.bytes = 0;
+  st = new SolverState();
+  st->B = B;
+  st->m = m;
+  st->N = N;
+  st->nchunk = (int)((N + kChunk - 1) / kChunk);
+  st->bytes = carve_bytes(B, m, N, st->nchunk);
+  cudaError_t e = cudaMalloc(&st->base, st->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete st;
+    set_error("solver workspace of %zu bytes could not be allocated", (size_t)carve_bytes(B, m, N, (int)((N + kChunk - 1) / kChunk)));
+    return VIE_ERR_OOM;
+  }
+  if ((e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming)) != cudaSuccess) {
+    release_state(st);
+    return cuda_status(e, "solver stream");
+  }
+  char* p = st->base;
+  const int nc = st->nchunk;
+  st->V = carve<float2>(p, (size_t)(m + 1) * B * N);
+  st->W = carve<float2>(p, (size_t)B * N);
+  st->d = carve<float2>(p, (size_t)B * N);
+  st->r32 = carve<float2>(p, (size_t)B * N);
+  st->H = carve<double2>(p, (size_t)B * m * (m + 1));
+  st->cs = carve<double2>(p, (size_t)B * m);
+  st->sn = carve<double2>(p, (size_t)B * m);
+  st->g = carve<double2>(p, (size_t)B * (m + 1));
+  st->coef = carve<double2>(p, (size_t)B * 129);
+  st->partial = carve<double2>(p, (size_t)B * 129 * nc);
+  st->nrm_partial = carve<double>(p, (size_t)B * nc);
+  st->nrm = carve<double>(p, B);
+  st->inv = carve<double>(p, B);
+  st->beta = carve<double>(p, B);
+  st->tol_abs = carve<double>(p, B);
+  st->rnorm = carve<double>(p, B);
+  st->bnorm = carve<double>(p, B);
+  carve<double>(p, B);
+  st->pb = carve<double>(p, (size_t)B * nc);
+  st->active = carve<int>(p, B);
+  st->iters = carve<int>(p, B);
+  st->want = carve<int>(p, B);
+  st->count_it = carve<int>(p, B);
+  st->count_mv = carve<int>(p, B);
+  st->x = carve<double2>(p, (size_t)B * N);
+  st->b64 = carve<double2>(p, (size_t)B * N);
+  st->r64 = carve<double2>(p, (size_t)B * N);
+  st->ax64 = carve<double2>(p, (size_t)B * N);
+  st->chi32 = carve<float2>(p, (size_t)N / 3);
+  st->chi64 = carve<double2>(p, (size_t)N / 3);
+  op->solver = st;
+  op->solve_ws.bytes = st->bytes;
+  *out = st;
+  return VIE_OK;
+}
+
+// One Arnoldi step k (CGS2) for all active RHS.
+static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, int k, int path,
+                        int adjoint, cudaStream_t s) {
+  const int B = st->B, m = st->m, nc = st->nchunk;
+  const long long N = st->N;
+  const float2* vk = st->V + (long long)k * B * N;
+  float2* w = st->W;
+  // w = A v_k
+  if (!adjoint)
+    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s));
+  else
+    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi, vk,
+                               st->active, s));
+  dim3 grid(nc, B);
+  const int rblocks = (k + 1 + 7) / 8;
+  for (int pass = 0; pass < 2; ++pass) {
+    dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, st->active);
+    reduce_dots_kernel<<<dim3(rblocks, B), 256, 0, s>>>(st->partial, k, nc, st->coef, st->H, m, pass,
+                                                        st->active);
+    update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc,
+                                            pass == 1 ? st->nrm_partial : nullptr, st->active);
+  }
+  reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, st->active);
+  givens_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m, B,
+                                             st->active, st->iters, st->tol_abs, st->count_it);
+  if (k + 1 < m + 1)
+    scale_into_kernel<<<grid, kThreads, 0, s>>>(w, st->V + (long long)(k + 1) * B * N, st->inv, N,
+                                                st->active);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "arnoldi");
+  return VIE_OK;
+}
+
+// End of a cycle: d += V y, then the true residual r = r32 - A d and the next cycle's start.
+static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int path, int adjoint,
+                      cudaStream_t s) {
+  const int B = st->B, m = st->m, nc = st->nchunk;
+  const long long N = st->N;
+  dim3 grid(nc, B);
+  backsolve_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
+  combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, B, N, st->iters);
+  // W = A d for the RHS still wanted
+  if (!adjoint)
+    VIE_TRY(matvec_impl<float>(op, st->d, st->W, B, path, 0, EPI_SUB | EPI_CHI, chi, st->d, st->want, s));
+  else
+    VIE_TRY(matvec_impl<float>(op, st->d, st->W, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi,
+                               st->d, st->want, s));
+  residual32_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->W, st->V, N, nc, st->nrm_partial, st->want);
+  reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
+  cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, m, B, st->want, st->active,
+                                                 st->iters, st->tol_abs, st->count_mv);
+  scale_into_kernel<<<grid, kThreads, 0, s>>>(st->V, st->V, st->inv, N, st->active);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "cycle tail");
+  return VIE_OK;
+}
+
+static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int path, int adjoint,
+                     bool use_graph, cudaStream_t s) {
+  if (!use_graph) {
+    for (int k = 0; k < st->m; ++k) VIE_TRY(arnoldi_step(op, st, chi, k, path, adjoint, s));
+    return cycle_tail(op, st, chi, path, adjoint, s);
+  }
+  // the graph bakes in every pointer it touches: rebuild it when any changes
+  if (st->exec && (st->graph_chi != chi || st->graph_stream != s || st->path != path ||
+                   st->graph_adjoint != adjoint || st->graph_ws != op->ws.ptr)) {
+    cudaGraphExecDestroy(st->exec);
+    st->exec = nullptr;
+  }
+  if (!st->exec) {
+    cudaGraph_t graph;
+    VIE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = VIE_OK;
+    for (int k = 0; k < st->m && rc == VIE_OK; ++k) rc = arnoldi_step(op, st, chi, k, path, adjoint, s);
+    if (rc == VIE_OK) rc = cycle_tail(op, st, chi, path, adjoint, s);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != VIE_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "graph capture");
+    e = cudaGraphInstantiate(&st->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      st->exec = nullptr;
+      return cuda_status(e, "graph instantiate");
+    }
+    st->graph_chi = chi;
+    st->graph_stream = s;
+    st->path = path;
+    st->graph_adjoint = adjoint;
+    st->graph_ws = op->ws.ptr;
+  }
+  VIE_CUDA(cudaGraphLaunch(st->exec, s));
+  return VIE_OK;
+}
+
+// FP32 GMRES on r32 (unit-norm rows) to relative tolerance `tol` for the RHS in `want`.
+static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint, double tol,
+                       int max_outer, bool use_graph, const std::vector<int>& want, cudaStream_t s) {
+  const int B = st->B, nc = st->nchunk;
+  const long long N = st->N;
+  dim3 grid(nc, B);
+  std::vector<double> tolv(B, tol);
+  VIE_CUDA(cudaMemcpyAsync(st->tol_abs, tolv.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+  VIE_CUDA(cudaMemcpyAsync(st->want, want.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+  // first cycle: d = 0, so the residual is r32 itself
+  norm32_kernel<<<grid, kThreads, 0, s>>>(st->r32, N, nc, st->nrm_partial, st->want);
+  reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
+  cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, st->m, B, st->want,
+                                                 st->active, st->iters, st->tol_abs, nullptr);
+  scale_into_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->V, st->inv, N, st->active);
+  VIE_CUDA(cudaGetLastError());
+  std::vector<int> act(B);
+  for (int cycle = 0; cycle < max_outer; ++cycle) {
+    VIE_CUDA(cudaMemcpyAsync(act.data(), st->active, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    int nact = 0;
+    for (int b = 0; b < B; ++b) nact += act[b];
+    if (nact == 0) return VIE_OK;
+    VIE_TRY(run_cycle(op, st, st->chi32, path, adjoint, use_graph, s));
+  }
+  return VIE_OK;
+}
+
+template <typename Tio>
+static void load_inputs(SolverState* st, const void* chi, const void* rhs, void* w, int B, long long nvox,
+                        int flags, cudaStream_t s) {
+  const long long total = 3LL * nvox * B;
+  const cx<Tio>* c = static_cast<const cx<Tio>*>(chi);
+  load_x_kernel<Tio><<<grid1(nvox), 256, 0, s>>>(c, st->chi64, nvox);
+  convert_kernel<float><<<grid1(nvox), 256, 0, s>>>(st->chi64, st->chi32, nvox);
+  load_rhs_kernel<Tio><<<grid1(total), 256, 0, s>>>(static_cast<const cx<Tio>*>(rhs), c, st->b64, nvox, B,
+                                                   (flags & VIE_SOLVE_RHS_INCIDENT) ? 1 : 0);
+  if (flags & VIE_SOLVE_X0)
+    load_x_kernel<Tio><<<grid1(total), 256, 0, s>>>(static_cast<const cx<Tio>*>(w), st->x, total);
+  else
+    cudaMemsetAsync(st->x, 0, total * sizeof(double2), s);
+}
+
+static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rhs, void* w, int B,
+                    int flags, int precision, const vie_solve_opts* o, vie_solve_info* info,
+                    cudaStream_t s);
+
+int solve_impl(const vie_op* op_c, const void* chi, const void* rhs, void* w, int B, int flags,
+               int precision, const vie_solve_opts* o, vie_solve_info* info, cudaStream_t caller) {
+  vie_op* op = const_cast<vie_op*>(op_c);
+  std::memset(info, 0, sizeof(*info));
+  const int m = o->restart;
+  const int path = o->path;
+  const int adjoint = (flags & VIE_SOLVE_ADJOINT) ? 1 : 0;
+  VIE_TRY(ensure_workspace(op, B));
+  SolverState* st = nullptr;
+  VIE_TRY(get_state(op, B, m, &st));
+  (void)path;
+  (void)adjoint;
+  VIE_CUDA(cudaEventRecord(st->ev_in, caller));
+  VIE_CUDA(cudaStreamWaitEvent(st->stream, st->ev_in, 0));
+  const int rc = solve_on(op, st, chi, rhs, w, B, flags, precision, o, info, st->stream);
+  cudaEventRecord(st->ev_out, st->stream);
+  cudaStreamWaitEvent(caller, st->ev_out, 0);
+  return rc;
+}
+
+static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rhs, void* w, int B,
+                    int flags, int precision, const vie_solve_opts* o, vie_solve_info* info,
+                    cudaStream_t s) {
+  const int path = o->path;
+  const int adjoint = (flags & VIE_SOLVE_ADJOINT) ? 1 : 0;
+  const long long nvox = (long long)op->n[0] * op->n[1] * op->n[2];
+  const long long N = st->N, total = N * B;
+  const int nc = st->nchunk;
+  dim3 grid(nc, B);
+  VIE_CUDA(cudaMemsetAsync(st->count_it, 0, B * sizeof(int), s));
+  VIE_CUDA(cudaMemsetAsync(st->count_mv, 0, B * sizeof(int), s));
+  if (precision == VIE_C64) load_inputs<float>(st, chi, rhs, w, B, nvox, flags, s);
+  else load_inputs<double>(st, chi, rhs, w, B, nvox, flags, s);
+  VIE_CUDA(cudaGetLastError());
+
+  std::vector<double> bn(B), rn(B);
+  std::vector<int> want(B, 1);
+  bool have_x = (flags & VIE_SOLVE_X0) != 0;
+  long long mv64 = 0;
+  int status = VIE_OK;
+  int step = 0;
+  for (;; ++step) {
+    if (have_x) {
+      if (!adjoint)
+        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path, 0, EPI_SUB | EPI_CHI, st->chi64, st->x,
+                                    nullptr, s));
+      else
+        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB,
+                                    st->chi64, st->x, nullptr, s));
+      mv64 += B;
+    }
+    residual64_kernel<<<grid, kThreads, 0, s>>>(st->b64, st->ax64, st->r64, N, nc, st->nrm_partial,
+                                                st->pb, have_x ? 1 : 0);
+    reduce_norm2_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->rnorm, B);
+    reduce_norm2_kernel<<<B, 32, 0, s>>>(st->pb, nc, st->bnorm, B);
+    VIE_CUDA(cudaGetLastError());
+    VIE_CUDA(cudaMemcpyAsync(rn.data(), st->rnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(bn.data(), st->bnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    bool finite = true;
+    for (int b = 0; b < B; ++b) {
+      const double rel = bn[b] > 0.0 ? rn[b] / bn[b] : 0.0;
+      if (!std::isfinite(rel)) finite = false;
+      want[b] = rel > o->tol ? 1 : 0;
+      worst = std::max(worst, rel);
+    }
+    if (step < 65) info->history[step] = worst;
+    info->relres = worst;
+    if (!finite) {
+      set_error("non-finite residual in refinement step %d", step);
+      status = VIE_ERR_NUMERIC;
+      break;
+    }
+    if (worst <= o->tol) {
+      info->converged = 1;
+      break;
+    }
+    if (step >= o->max_refine || (!o->refine && step >= 1)) {
+      set_error("relative residual %.3e above %.3e after %d refinement steps", worst, o->tol, step);
+      status = VIE_ERR_NO_CONVERGENCE;
+      break;
+    }
+    VIE_CUDA(cudaMemcpyAsync(st->want, want.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    to_inner_kernel<<<grid, kThreads, 0, s>>>(st->r64, st->rnorm, st->r32, st->d, N, st->want);
+    const double itol = o->refine ? std::max(o->inner_tol, 1e-7) : o->tol;
+    VIE_TRY(inner_gmres(op, st, path, adjoint, itol, o->max_outer, o->use_graph != 0, want, s));
+    accumulate_kernel<<<grid, kThreads, 0, s>>>(st->x, st->d, st->rnorm, N, st->want);
+    VIE_CUDA(cudaGetLastError());
+    have_x = true;
+  }
+  info->refine_steps = step;
+  std::vector<int> ci(B), cm(B);
+  VIE_CUDA(cudaMemcpyAsync(ci.data(), st->count_it, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA(cudaMemcpyAsync(cm.data(), st->count_mv, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (precision == VIE_C64)
+    convert_kernel<float><<<grid1(total), 256, 0, s>>>(st->x, static_cast<float2*>(w), total);
+  else
+    VIE_CUDA(cudaMemcpyAsync(w, st->x, total * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+  long long it = 0, mv = mv64;
+  for (int b = 0; b < B; ++b) {
+    it += ci[b];
+    mv += ci[b] + cm[b];
+  }
+  info->iterations = (int)std::min<long long>(it, 2147483647LL);
+  info->matvecs = (int)std::min<long long>(mv, 2147483647LL);
+  return status;
+}

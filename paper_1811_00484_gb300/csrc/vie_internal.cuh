@@ -173,6 +173,8 @@ int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, c
                    vie_op** out);
 int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s);
 int op_tables(vie_op* op);   // FFT plans and root tables of op->P
+int line_fft_init_attributes();
+int fused_init_attributes();
 
 // solver (solve.cu)
 int solve_impl(const vie_op* op, const void* chi, const void* rhs, void* w, int B, int flags,
