@@ -10,7 +10,6 @@ the error by 1e-7.  Tight targets use complex128 inputs and outputs: a
 complex64 solution is rounded to FP32 on output, which alone leaves a
 relative residual of a few 1e-8 (bounded here by 5e-7).
 """
-C128 = torch.complex128
 import numpy as np
 import pytest
 import torch
@@ -25,6 +24,7 @@ from oracle import matvec as M
 
 vie = pytest.importorskip("paper_1811_00484_gb300")
 pytestmark = pytest.mark.gpu
+C128 = torch.complex128
 
 
 def dev(a, dtype=torch.complex64):
