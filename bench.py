@@ -1,0 +1,309 @@
+"""Benchmark of the Tucker-compressed FFT-VIE solve on GB300.
+
+Workload: the 64^3-voxel solve (128^3 padded), 5 mm voxels at 298 MHz,
+seeded ellipsoidal tissue contrast, x-polarised plane wave, HOSVD at 1e-6,
+GMRES(50) to a relative residual of 1e-6 with FP64 iterative refinement.
+One step = one complete solve (pad/FFT, Tucker rebuild + product, inverse
+FFT/crop, contrast, Arnoldi, refinement residuals).  `value` = operator
+applications (matvecs) per second over the timed solves; the same solves on
+the uncompressed-spectra path, isolated matvec rates of both paths and the
+FP64 CPU oracle are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tucker-VIE matvecs/s & GMRES solve time vs uncompressed FFT path, same GB300"
+UNIT = "matvecs/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_matvec_rate(wl, seconds=15.0, max_matvecs=None):
+    """Oracle Tucker matvecs (FP64 numpy: FFT, rebuilt spectra, product) per second."""
+    import numpy as np
+    from oracle import embed, hosvd, kernel, matvec
+
+    k0 = kernel.wavenumber(wl.freq_hz)
+    Ghat = embed.green_spectra(kernel.toeplitz_tensor(*wl.n, wl.h, k0), *wl.n)
+    rebuilt = hosvd.rebuild_components(hosvd.compress_components(Ghat, wl.tol_svd))
+    w = wl.einc * wl.chi
+    count, t0 = 0, time.perf_counter()
+    while True:
+        w = matvec.apply_system(rebuilt, wl.chi, w / np.linalg.norm(w))
+        count += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_matvecs and count >= max_matvecs):
+            break
+    return count / el, count, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    wl = workloads.solve_n64() if args.n == 64 else workloads.make("custom", args.n, 1, incident="plane")
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_matvec_rate(wl, seconds=0.0, max_matvecs=1)
+    rates, t_total, n_total = [], 0.0, 0
+    for _ in range(args.steps):
+        r, c, el = oracle_matvec_rate(wl, seconds=5.0)
+        rates.append(r)
+        t_total += el
+        n_total += c
+    value = n_total / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": f"oracle Tucker matvecs, {wl.n[0]}^3 voxels ({2*wl.n[0]}^3 padded), "
+                                   "tol 1e-6, plane wave", "parallelism": "none"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_total} FP64 oracle system matvecs over {t_total:.1f} s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    wl = workloads.solve_n64() if args.n == 64 else workloads.make("custom", args.n, 1, incident="plane")
+    n = wl.n
+    op = vie.Operator(n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=True)
+    info = op.info()
+    chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
+    einc = torch.from_numpy(wl.einc.astype(np.complex64)).cuda()
+    chi_h = torch.from_numpy(wl.chi.astype(np.complex64)).pin_memory()
+    einc_h = torch.from_numpy(wl.einc.astype(np.complex64)).pin_memory()
+    w_h = torch.empty_like(einc_h).pin_memory()
+    solve_kw = dict(tol=1e-6, restart=50, max_outer=200, max_refine=20)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_solves(path, steps):
+        mv = 0
+        its = []
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.nvtx.range_push(f"{path}_solve")
+        start.record()
+        for _ in range(steps):
+            w, inf = op.solve(chi, einc, path=path, **solve_kw)
+            mv += inf["matvecs"]
+            its.append(inf)
+        stop.record()
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        return start.elapsed_time(stop) / 1e3, mv, its
+
+    for _ in range(args.warmup):
+        op.solve(chi, einc, **solve_kw)
+        op.solve(chi, einc, path="uncompressed", **solve_kw)
+
+    with ClockSampler(local) as clk:
+        t_tucker, mv_tucker, it_tucker = timed_solves("tucker", args.steps)
+    clocks = clk.summary()
+    t_unc, mv_unc, it_unc = timed_solves("uncompressed", args.steps)
+
+    # end to end: host buffers in, host solution out, through the same C-ABI solve
+    barrier()
+    e2e_start = time.perf_counter()
+    mv_e2e = 0
+    for _ in range(args.steps):
+        c_d = chi_h.to("cuda", non_blocking=True)
+        e_d = einc_h.to("cuda", non_blocking=True)
+        w, inf = op.solve(c_d, e_d, **solve_kw)
+        mv_e2e += inf["matvecs"]
+        w_h.copy_(w, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    t_e2e = time.perf_counter() - e2e_start
+
+    # isolated matvec rates (B = 1), L2 flushed between timed launches
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    J = torch.from_numpy(wl.J.astype(np.complex64)).cuda()
+
+    def matvec_rate(path, reps=20):
+        for _ in range(3):
+            op.matvec(J, path=path)
+        torch.cuda.nvtx.range_push(f"{path}_matvec")
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            op.matvec(J, path=path)
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        torch.cuda.nvtx.range_pop()
+        return reps / (tot / 1e3), tot / reps
+
+    mv_rate_t, mv_ms_t = matvec_rate("tucker")
+    mv_rate_u, mv_ms_u = matvec_rate("uncompressed")
+
+    # accuracy of one matvec against the oracle (FP64 numpy), rank 0 only
+    acc = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import embed, kernel, matvec
+        k0 = kernel.wavenumber(wl.freq_hz)
+        Ghat = embed.green_spectra(kernel.toeplitz_tensor(*n, wl.h, k0), *n)
+        ref = matvec.matvec_fft(Ghat, wl.J)
+        y = op.matvec(J).cpu().numpy().astype(np.complex128)
+        acc = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+        rate, count, el = oracle_matvec_rate(wl, seconds=15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{count} FP64 oracle system matvecs ({n[0]}^3, Tucker-rebuilt spectra) "
+                         f"in {el:.1f} s"}
+
+    value = world * mv_tucker / t_tucker
+    peak, peak_kind = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_tucker / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"solve {n[0]}^3 voxels ({2*n[0]}^3 padded), plane wave, HOSVD 1e-6, "
+                               "GMRES(50) to 1e-6 + FP64 refinement",
+                   "global_batch": world, "parallelism": f"replicas x{world}",
+                   "l2": "solve working set (Krylov basis 51 x 6.3 MB) > L2; isolated matvecs flush L2"},
+        "solve": {"tucker_ms": 1e3 * t_tucker / args.steps,
+                  "uncompressed_ms": 1e3 * t_unc / args.steps,
+                  "iterations": it_tucker[-1]["iterations"], "refine_steps": it_tucker[-1]["refine_steps"],
+                  "relres": it_tucker[-1]["relres"],
+                  "uncompressed_matvecs_per_s": world * mv_unc / t_unc},
+        "matvec": {"tucker_per_s": mv_rate_t, "tucker_ms": mv_ms_t,
+                   "uncompressed_per_s": mv_rate_u, "uncompressed_ms": mv_ms_u,
+                   "rel_err_vs_oracle": acc},
+        "memory": {"tucker_bytes": info["tucker_bytes"], "uncompressed_bytes": info["uncompressed_bytes"],
+                   "ranks": info["ranks"]},
+        "clocks": clocks,
+        "e2e": {"value": world * mv_e2e / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": chi_h.numel() * 8 + einc_h.numel() * 8,
+                "d2h_bytes_per_step": w_h.numel() * 8},
+        "cpu_baseline": cpu,
+        "roofline": None,
+        "gpu_launches": None,
+        "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    op.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
