@@ -38,6 +38,10 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="solve", choices=["solve", "matvec"],
+                   help="matvec: only K timed batched matvecs (a small command for profilers)")
+    p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
+    p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
     return p.parse_args()
 
 
@@ -158,6 +162,34 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_matvec_mode(args):
+    """K batched matvecs of the bench workload, nothing else (for ncu captures)."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    wl = workloads.make("matvec", args.n, seed=1, B=args.batch, tol_svd=1e-6)
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed")
+    J = torch.from_numpy(wl.J.astype(np.complex64)).cuda()
+    Y = torch.empty_like(J)
+    for _ in range(args.warmup):
+        op.matvec(J, path=args.path, out=Y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_matvec")
+    a.record()
+    for _ in range(args.steps):
+        op.matvec(J, path=args.path, out=Y)
+    b.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"mode": "matvec", "n": args.n, "batch": args.batch, "path": args.path,
+                      "ms_per_matvec_batch": ms, "matvecs_per_s": args.batch / (ms * 1e-3)}))
+
+
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
@@ -165,6 +197,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "matvec":
+        return run_matvec_mode(args)
     import numpy as np
     import torch
 
@@ -213,7 +247,9 @@ def main():
         op.solve(chi, einc, path="uncompressed", **solve_kw)
 
     with ClockSampler(local) as clk:
+        vie.profile_start()
         t_tucker, mv_tucker, it_tucker = timed_solves("tucker", args.steps)
+        kern = vie.profile_stop()
     clocks = clk.summary()
     t_unc, mv_unc, it_unc = timed_solves("uncompressed", args.steps)
 
@@ -253,6 +289,10 @@ def main():
 
     mv_rate_t, mv_ms_t = matvec_rate("tucker")
     mv_rate_u, mv_ms_u = matvec_rate("uncompressed")
+    # fused kernel alone at B = 1 (isolated matvecs, L2 flushed), for its HBM fraction
+    vie.profile_start()
+    matvec_rate("tucker", reps=10)
+    kern_mv = vie.profile_stop()
 
     # accuracy of one matvec against the oracle (FP64 numpy), rank 0 only
     acc = None
@@ -271,6 +311,26 @@ def main():
 
     value = world * mv_tucker / t_tucker
     peak, peak_kind = measured_peaks()
+
+    def gbs(e):
+        return e["bytes"] / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else 0.0
+
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in kern.values())), 4),
+                   "GBps": round(gbs(v), 1)} for k, v in kern.items()}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(gbs(d), 1), "peak": peak,
+                "unit": "GB/s", "frac": round(gbs(d) / peak, 4), "traffic": None,
+                "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    f = kern_mv.get("fused_tucker")
+    roofline_fused = None
+    if f:
+        roofline_fused = {"kernel": "fused_tucker (isolated matvec, B=1, L2 flushed)", "bound": "hbm",
+                          "achieved": round(gbs(f), 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(gbs(f) / peak, 4), "avg_launch_us": 1e3 * f["ms"] / f["launches"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_tucker / args.steps, "higher_is_better": True,
@@ -294,9 +354,10 @@ def main():
                 "h2d_bytes_per_step": chi_h.numel() * 8 + einc_h.numel() * 8,
                 "d2h_bytes_per_step": w_h.numel() * 8},
         "cpu_baseline": cpu,
-        "roofline": None,
-        "gpu_launches": None,
-        "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+        "roofline": roofline,
+        "roofline_fused": roofline_fused,
+        "kernels": kernels,
+        "gpu_launches": int(sum(v["launches"] for v in kern.values())),
     }
     if rank == 0:
         print(json.dumps(line))

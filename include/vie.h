@@ -231,6 +231,27 @@ int vie_contrast_gradient(const vie_op* op, const void* lam, const void* E,
 int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* out,
                         int precision, void* stream);
 
+/*
+ * Benchmark instrumentation (no counterpart in the paper).  Between
+ * vie_profile_start() and vie_profile_stop() every launch of the library's
+ * kernel families is bracketed by CUDA events on the stream it runs on
+ * (inside CUDA graphs as event nodes read after each replay), and kernels
+ * add the algorithmic bytes they move for active right-hand sides to a
+ * per-family device counter.  vie_profile_stop() synchronises the device
+ * and fills up to max_entries host records (*count of them), one per family
+ * that ran: name, launches, total milliseconds, total algorithmic bytes.
+ * Profiling adds two event records per launch; it is off by default.
+ */
+typedef struct vie_profile_entry {
+    char name[32];
+    long long launches;
+    double ms;
+    double bytes;
+} vie_profile_entry;
+
+int vie_profile_start(void);
+int vie_profile_stop(vie_profile_entry* out, int max_entries, int* count);
+
 /* Release `op` and everything it owns (NULL is allowed). */
 void vie_destroy(vie_op* op);
 

@@ -35,7 +35,8 @@ COMPONENTS = ("xx", "xy", "xz", "yy", "yz", "zz")
 EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spectrum",
            "vie_reserve", "vie_matvec", "vie_matvec_adjoint", "vie_apply_system",
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
-           "vie_destroy", "vie_status_string", "vie_last_error")
+           "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
+           "vie_profile_stop")
 
 
 class VieError(RuntimeError):
@@ -60,6 +61,11 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int), ("path", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -90,6 +96,8 @@ def _load():
         "vie_contrast_gradient": [vp, vp, vp, vp, ci, cd, ci, vp],
         "vie_incident_dipole": [vp, pd, ci, vp, ci, vp],
         "vie_destroy": [vp],
+        "vie_profile_start": [],
+        "vie_profile_stop": [ctypes.POINTER(ProfileEntry), ci, ctypes.POINTER(ci)],
         "vie_status_string": [ci],
         "vie_last_error": [],
     }
@@ -292,6 +300,20 @@ class Operator:
                                        B, _dev(out, "out"), _precision(out), _stream()),
                "vie_incident_dipole")
         return out
+
+
+def profile_start():
+    """Start per-kernel-family event timing (vie_profile_start)."""
+    _check(lib.vie_profile_start(), "vie_profile_start")
+
+
+def profile_stop():
+    """Stop timing; {family: {"launches", "ms", "bytes"}} of the families that ran."""
+    buf = (ProfileEntry * 32)()
+    n = ctypes.c_int()
+    _check(lib.vie_profile_stop(buf, 32, ctypes.byref(n)), "vie_profile_stop")
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms,
+                                   "bytes": buf[i].bytes} for i in range(n.value)}
 
 
 def green_spectrum(n, h, freq_hz, c, self_term="full", device="cuda"):

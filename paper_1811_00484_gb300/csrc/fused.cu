@@ -27,10 +27,14 @@ template <typename T> struct SlabArgs {
   cx<T>* slab;
   long long slab_stride;
   int r2max, r3max;
+  unsigned long long* prof;
+  unsigned long long prof_launch_bytes;
 };
 
 template <typename T>
 __global__ void __launch_bounds__(256) slab_core_kernel(const SlabArgs<T> a) {
+  if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(a.prof, a.prof_launch_bytes);
   using C = cx<T>;
   const int k1 = blockIdx.x, c = blockIdx.y;
   const int r1 = a.r1[c], r2 = a.r2[c], r3 = a.r3[c];
@@ -59,13 +63,20 @@ template <typename T> struct FusedArgs {
   const int* active;           // per RHS, nullptr = all
   int lines_per_round;         // z-lines (x3 components) held in shared memory at once
   int ld;                      // shared-memory line stride
+  unsigned long long* prof;    // profiler byte counter (nullptr = off)
+  unsigned long long prof_rhs_bytes, prof_launch_bytes;
 };
 
 template <typename T, bool STORED>
-__global__ void __launch_bounds__(256) fused_z_kernel(const FusedArgs<T> a) {
+__global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nth = blockDim.x;
+  if (a.prof != nullptr && blockIdx.x == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
   const int P3 = a.P3, n3 = a.n3, ld = a.ld, H3 = a.H3;
   const int g = blockIdx.x;
   const int k1 = g / a.H2, k2 = g % a.H2;
@@ -187,6 +198,11 @@ static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
     return VIE_ERR_ARG;
   }
   a.lines_per_round = LR;
+  const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
+  a.prof = prof_bytes(fam);
+  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(cx<T>);       // 3 components read + written
+  a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(cx<T>) : 0ull;
+  ProfScope ps(fam, s);
   fused_z_kernel<T, STORED><<<a.H1 * a.H2, 256, fused_smem(a, LR), s>>>(a);
   return VIE_OK;
 }
@@ -216,7 +232,10 @@ int launch_slab_cores(const vie_op* op, cudaStream_t s) {
   a.slab_stride = (long long)op->slab_stride;
   a.r2max = op->rmax[1];
   a.r3max = op->rmax[2];
+  a.prof = prof_bytes(PF_SLAB);
+  a.prof_launch_bytes = 6ull * op->slab_stride * sizeof(cx<T>);
   dim3 grid(op->H[0], 6);
+  ProfScope ps(PF_SLAB, s);
   vie::slab_core_kernel<T><<<grid, 256, 0, s>>>(a);
   return VIE_OK;
 }

@@ -13,7 +13,7 @@
 namespace vie {
 
 template <typename T, int TW>
-__global__ void __launch_bounds__(256) line_fft_kernel(const LineArgs<T> a) {
+__global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.plan.N;
@@ -26,6 +26,8 @@ __global__ void __launch_bounds__(256) line_fft_kernel(const LineArgs<T> a) {
   const int bb = blockIdx.z;
   if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
   const int tid = threadIdx.x, nth = blockDim.x;
+  if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0)
+    atomicAdd(a.prof, a.prof_batch_bytes);
   const int ncols = min(TW, a.ncol - c0);
 
   for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
@@ -67,8 +69,10 @@ __global__ void __launch_bounds__(256) line_fft_kernel(const LineArgs<T> a) {
 }
 
 template <typename T, int TW>
-static void launch_tw(const LineArgs<T>& a, size_t smem, cudaStream_t s) {
+static void launch_tw(LineArgs<T> a, size_t smem, cudaStream_t s) {
   dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
   line_fft_kernel<T, TW><<<grid, 256, smem, s>>>(a);
 }
 

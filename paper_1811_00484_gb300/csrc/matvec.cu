@@ -87,6 +87,9 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
     a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
     a.batch_per_rhs = 3;
     a.active = active;
+    a.prof_family = PF_LINE_X;
+    a.prof_batch_bytes = (unsigned long long)((n1 + P1) * n2 * n3 * sizeof(C)) +
+                         ((a.flags & PRO_CHI) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull);
     launch_line_fft<T>(a, s);
   }
   // y stage: T1 -> T2
@@ -106,6 +109,8 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
     a.out_bs = P1 * P2 * n3; a.out_os = P2 * n3; a.out_ls = n3; a.out_cs = 1;
     a.batch_per_rhs = 3;
     a.active = active;
+    a.prof_family = PF_LINE_Y;
+    a.prof_batch_bytes = (unsigned long long)((n2 + P2) * P1 * n3 * sizeof(C));
     launch_line_fft<T>(a, s);
   }
   // z stage fused with the rebuild and the product
@@ -128,6 +133,8 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
     a.out_bs = P1 * n2 * n3; a.out_os = n2 * n3; a.out_ls = n3; a.out_cs = 1;
     a.batch_per_rhs = 3;
     a.active = active;
+    a.prof_family = PF_LINE_IY;
+    a.prof_batch_bytes = (unsigned long long)((n2 + P2) * P1 * n3 * sizeof(C));
     launch_line_fft<T>(a, s);
   }
   // inverse x stage: T1 -> out (crop, scale, epilogue)
@@ -152,6 +159,10 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
     a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
     a.batch_per_rhs = 3;
     a.active = active;
+    a.prof_family = PF_LINE_IX;
+    a.prof_batch_bytes = (unsigned long long)((P1 + n1) * n2 * n3 * sizeof(C)) +
+                         ((a.flags & (EPI_SUB | EPI_ADD)) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull) +
+                         ((a.flags & EPI_CHI) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull);
     launch_line_fft<T>(a, s);
   }
   cudaError_t e = cudaGetLastError();

@@ -348,6 +348,7 @@ static void fft3d_f64(const vie_op* op, double2* a, cudaStream_t s) {
     L.scale = 1.0;
     L.nbatch = 1;
     L.batch_per_rhs = 1;
+    L.prof_family = PF_SETUP;
     if (axis == 0) {          // lines along x, columns z, other y
       L.nother = (int)P2; L.ncol = (int)P3;
       L.in_os = L.out_os = P3; L.in_ls = L.out_ls = P2 * P3; L.in_cs = L.out_cs = 1;

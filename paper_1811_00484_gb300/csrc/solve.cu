@@ -33,13 +33,18 @@ __device__ __forceinline__ double2 wsum(double2 v) {
   return v;
 }
 
-// partial[b][i][chunk] = sum over the chunk of conj(V_i[b]) w[b], i = 0..k
+// partial[b][i][chunk] = sum over the chunk of conj(V_i[b]) w[b], i = 0..k.
+// Each thread forms its kPer products in FP32 (the data are FP32); the sums
+// across threads, warps and chunks are FP64 (GB300's FP64 rate is far below
+// its FP32 rate, so FP64 is kept out of the per-element work).
 __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict__ V,
                                                         const float2* __restrict__ w, int k, int B,
                                                         long long N, int nchunk, double2* partial,
-                                                        const int* active) {
+                                                        const int* active, unsigned long long* prof,
+                                                        unsigned long long prof_bytes) {
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (!active[b]) return;
+  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   __shared__ double2 red[kThreads / 32][129];
   const long long base = (long long)chunk * kChunk;
   float2 wv[kPer];
@@ -51,17 +56,17 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = 0; i <= k; ++i) {
     const float2* vi = V + ((long long)i * B + b) * N;
-    double2 acc = make_double2(0.0, 0.0);
+    float ax = 0.f, ay = 0.f;
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
       const long long idx = base + e * kThreads + threadIdx.x;
       if (idx < N) {
         const float2 v = vi[idx];
-        acc.x += (double)v.x * wv[e].x + (double)v.y * wv[e].y;
-        acc.y += (double)v.x * wv[e].y - (double)v.y * wv[e].x;
+        ax = fmaf(v.x, wv[e].x, fmaf(v.y, wv[e].y, ax));
+        ay = fmaf(v.x, wv[e].y, fmaf(-v.y, wv[e].x, ay));
       }
     }
-    acc = wsum(acc);
+    double2 acc = wsum(make_double2((double)ax, (double)ay));
     if (lane == 0) red[warp][i] = acc;
   }
   __syncthreads();
@@ -76,9 +81,11 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict
 __global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restrict__ V, float2* w,
                                                           const double2* coef, int k, int B,
                                                           long long N, int nchunk, double* nrm_partial,
-                                                          const int* active) {
+                                                          const int* active, unsigned long long* prof,
+                                                          unsigned long long prof_bytes) {
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (!active[b]) return;
+  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   __shared__ float2 c[129];
   __shared__ double red[kThreads / 32];
   for (int i = threadIdx.x; i <= k; i += kThreads) {
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restri
   }
   __syncthreads();
   const long long base = (long long)chunk * kChunk;
-  double nrm = 0.0;
+  float nrm32 = 0.f;
 #pragma unroll
   for (int e = 0; e < kPer; ++e) {
     const long long idx = base + e * kThreads + threadIdx.x;
@@ -99,10 +106,11 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restri
         acc.y -= c[i].x * v.y + c[i].y * v.x;
       }
       w[(long long)b * N + idx] = acc;
-      nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
+      nrm32 = fmaf(acc.x, acc.x, fmaf(acc.y, acc.y, nrm32));
     }
   }
   if (nrm_partial) {
+    double nrm = (double)nrm32;
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
     __syncthreads();
@@ -148,14 +156,15 @@ __global__ void __launch_bounds__(kThreads) norm32_kernel(const float2* v, long 
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (active && !active[b]) return;
   __shared__ double red[kThreads / 32];
-  double s = 0.0;
+  float s32 = 0.f;
   for (int e = 0; e < kPer; ++e) {
     const long long idx = (long long)chunk * kChunk + e * kThreads + threadIdx.x;
     if (idx < N) {
       const float2 x = v[(long long)b * N + idx];
-      s += (double)x.x * x.x + (double)x.y * x.y;
+      s32 = fmaf(x.x, x.x, fmaf(x.y, x.y, s32));
     }
   }
+  double s = (double)s32;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -274,16 +283,17 @@ __global__ void __launch_bounds__(kThreads) residual32_kernel(const float2* rhs,
   const int b = blockIdx.y, chunk = blockIdx.x;
   if (!want[b]) return;
   __shared__ double red[kThreads / 32];
-  double s = 0.0;
+  float s32 = 0.f;
   for (int e = 0; e < kPer; ++e) {
     const long long idx = (long long)chunk * kChunk + e * kThreads + threadIdx.x;
     if (idx < N) {
       const long long o = (long long)b * N + idx;
       const float2 v = make_float2(rhs[o].x - ad[o].x, rhs[o].y - ad[o].y);
       r[o] = v;
-      s += (double)v.x * v.x + (double)v.y * v.y;
+      s32 = fmaf(v.x, v.x, fmaf(v.y, v.y, s32));
     }
   }
+  double s = (double)s32;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -459,11 +469,21 @@ struct SolverState {
   const void* graph_ws = nullptr;
   cudaStream_t graph_stream = nullptr;
   int graph_adjoint = -1;
+  int graph_prof = -1;                        // profiler epoch the graph was captured in
+  std::vector<ProfEventPair> graph_events;    // event nodes of the captured graph
+  bool graph_pending = false;                 // a replay ran since the last harvest
 };
+
+static void drop_graph(SolverState* st) {
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  st->exec = nullptr;
+  prof_release_pairs(st->graph_events);
+}
 
 static void release_state(SolverState* st) {
   if (!st) return;
-  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  drop_graph(st);
   if (st->stream) {
     cudaStreamSynchronize(st->stream);
     cudaStreamDestroy(st->stream);
@@ -589,19 +609,33 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
                                st->active, s));
   dim3 grid(nc, B);
   const int rblocks = (k + 1 + 7) / 8;
+  const unsigned long long vec = (unsigned long long)N * sizeof(float2);
   for (int pass = 0; pass < 2; ++pass) {
-    dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, st->active);
-    reduce_dots_kernel<<<dim3(rblocks, B), 256, 0, s>>>(st->partial, k, nc, st->coef, st->H, m, pass,
-                                                        st->active);
-    update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc,
-                                            pass == 1 ? st->nrm_partial : nullptr, st->active);
+    {
+      ProfScope ps(PF_DOTS, s);
+      dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, st->active,
+                                            prof_bytes(PF_DOTS), (k + 2) * vec);
+    }
+    {
+      ProfScope ps(PF_SMALL, s);
+      reduce_dots_kernel<<<dim3(rblocks, B), 256, 0, s>>>(st->partial, k, nc, st->coef, st->H, m,
+                                                          pass, st->active);
+    }
+    {
+      ProfScope ps(PF_UPDATE, s);
+      update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc,
+                                              pass == 1 ? st->nrm_partial : nullptr, st->active,
+                                              prof_bytes(PF_UPDATE), (k + 3) * vec);
+    }
   }
-  reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, st->active);
-  givens_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m, B,
-                                             st->active, st->iters, st->tol_abs, st->count_it);
-  if (k + 1 < m + 1)
+  {
+    ProfScope ps(PF_SMALL, s);
+    reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, st->active);
+    givens_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m,
+                                               B, st->active, st->iters, st->tol_abs, st->count_it);
     scale_into_kernel<<<grid, kThreads, 0, s>>>(w, st->V + (long long)(k + 1) * B * N, st->inv, N,
                                                 st->active);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "arnoldi");
   return VIE_OK;
@@ -613,19 +647,26 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
   const int B = st->B, m = st->m, nc = st->nchunk;
   const long long N = st->N;
   dim3 grid(nc, B);
-  backsolve_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
-  combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, B, N, st->iters);
+  {
+    ProfScope ps(PF_SMALL, s);
+    backsolve_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
+    combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, B, N, st->iters);
+  }
   // W = A d for the RHS still wanted
   if (!adjoint)
     VIE_TRY(matvec_impl<float>(op, st->d, st->W, B, path, 0, EPI_SUB | EPI_CHI, chi, st->d, st->want, s));
   else
     VIE_TRY(matvec_impl<float>(op, st->d, st->W, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi,
                                st->d, st->want, s));
-  residual32_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->W, st->V, N, nc, st->nrm_partial, st->want);
-  reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
-  cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, m, B, st->want, st->active,
-                                                 st->iters, st->tol_abs, st->count_mv);
-  scale_into_kernel<<<grid, kThreads, 0, s>>>(st->V, st->V, st->inv, N, st->active);
+  {
+    ProfScope ps(PF_SMALL, s);
+    residual32_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->W, st->V, N, nc, st->nrm_partial,
+                                                st->want);
+    reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
+    cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, m, B, st->want,
+                                                   st->active, st->iters, st->tol_abs, st->count_mv);
+    scale_into_kernel<<<grid, kThreads, 0, s>>>(st->V, st->V, st->inv, N, st->active);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "cycle tail");
   return VIE_OK;
@@ -639,16 +680,18 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
   }
   // the graph bakes in every pointer it touches: rebuild it when any changes
   if (st->exec && (st->graph_chi != chi || st->graph_stream != s || st->path != path ||
-                   st->graph_adjoint != adjoint || st->graph_ws != op->ws.ptr)) {
-    cudaGraphExecDestroy(st->exec);
-    st->exec = nullptr;
+                   st->graph_adjoint != adjoint || st->graph_ws != op->ws.ptr ||
+                   st->graph_prof != prof_epoch())) {
+    drop_graph(st);
   }
   if (!st->exec) {
     cudaGraph_t graph;
     VIE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    prof_set_capture_sink(&st->graph_events);
     int rc = VIE_OK;
     for (int k = 0; k < st->m && rc == VIE_OK; ++k) rc = arnoldi_step(op, st, chi, k, path, adjoint, s);
     if (rc == VIE_OK) rc = cycle_tail(op, st, chi, path, adjoint, s);
+    prof_set_capture_sink(nullptr);
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (rc != VIE_OK) {
       if (e == cudaSuccess) cudaGraphDestroy(graph);
@@ -666,9 +709,17 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
     st->path = path;
     st->graph_adjoint = adjoint;
     st->graph_ws = op->ws.ptr;
+    st->graph_prof = prof_epoch();
   }
   VIE_CUDA(cudaGraphLaunch(st->exec, s));
+  st->graph_pending = true;
   return VIE_OK;
+}
+
+// after a synchronisation: read the event nodes of the graph replay that just ran
+static void harvest_graph(SolverState* st) {
+  if (st->graph_pending) prof_harvest_graph(st->graph_events);
+  st->graph_pending = false;
 }
 
 // FP32 GMRES on r32 (unit-norm rows) to relative tolerance `tol` for the RHS in `want`.
@@ -691,11 +742,14 @@ static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint,
   for (int cycle = 0; cycle < max_outer; ++cycle) {
     VIE_CUDA(cudaMemcpyAsync(act.data(), st->active, B * sizeof(int), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaStreamSynchronize(s));
+    harvest_graph(st);
     int nact = 0;
     for (int b = 0; b < B; ++b) nact += act[b];
     if (nact == 0) return VIE_OK;
     VIE_TRY(run_cycle(op, st, st->chi32, path, adjoint, use_graph, s));
   }
+  VIE_CUDA(cudaStreamSynchronize(s));
+  harvest_graph(st);
   return VIE_OK;
 }
 
@@ -769,10 +823,13 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
                                     st->chi64, st->x, nullptr, s));
       mv64 += B;
     }
-    residual64_kernel<<<grid, kThreads, 0, s>>>(st->b64, st->ax64, st->r64, N, nc, st->nrm_partial,
-                                                st->pb, have_x ? 1 : 0);
-    reduce_norm2_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->rnorm, B);
-    reduce_norm2_kernel<<<B, 32, 0, s>>>(st->pb, nc, st->bnorm, B);
+    {
+      ProfScope ps(PF_FP64, s);
+      residual64_kernel<<<grid, kThreads, 0, s>>>(st->b64, st->ax64, st->r64, N, nc, st->nrm_partial,
+                                                  st->pb, have_x ? 1 : 0);
+      reduce_norm2_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->rnorm, B);
+      reduce_norm2_kernel<<<B, 32, 0, s>>>(st->pb, nc, st->bnorm, B);
+    }
     VIE_CUDA(cudaGetLastError());
     VIE_CUDA(cudaMemcpyAsync(rn.data(), st->rnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaMemcpyAsync(bn.data(), st->bnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -802,10 +859,19 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
       break;
     }
     VIE_CUDA(cudaMemcpyAsync(st->want, want.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
-    to_inner_kernel<<<grid, kThreads, 0, s>>>(st->r64, st->rnorm, st->r32, st->d, N, st->want);
-    const double itol = o->refine ? std::max(o->inner_tol, 1e-7) : o->tol;
+    {
+      ProfScope ps(PF_FP64, s);
+      to_inner_kernel<<<grid, kThreads, 0, s>>>(st->r64, st->rnorm, st->r32, st->d, N, st->want);
+    }
+    // each refinement step only needs to bring the residual from `worst` to `tol`
+    // (with a factor 4 of headroom), never tighter than inner_tol or FP32 allows
+    const double need = 0.25 * o->tol / std::max(worst, 1e-300);
+    const double itol = o->refine ? std::min(0.5, std::max({o->inner_tol, need, 1e-7})) : o->tol;
     VIE_TRY(inner_gmres(op, st, path, adjoint, itol, o->max_outer, o->use_graph != 0, want, s));
-    accumulate_kernel<<<grid, kThreads, 0, s>>>(st->x, st->d, st->rnorm, N, st->want);
+    {
+      ProfScope ps(PF_FP64, s);
+      accumulate_kernel<<<grid, kThreads, 0, s>>>(st->x, st->d, st->rnorm, N, st->want);
+    }
     VIE_CUDA(cudaGetLastError());
     have_x = true;
   }

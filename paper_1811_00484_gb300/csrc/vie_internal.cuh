@@ -70,6 +70,33 @@ enum {
   EPI_CHI = 32       // multiply the result by chi before EPI_SUB
 };
 
+// ---------------------------------------------------------------------------
+// kernel-family profiler (profiler.cu)
+// ---------------------------------------------------------------------------
+enum {
+  PF_LINE_X = 0, PF_LINE_Y, PF_FUSED_TUCKER, PF_FUSED_STORED, PF_LINE_IY, PF_LINE_IX, PF_SLAB,
+  PF_DOTS, PF_UPDATE, PF_SMALL, PF_FP64, PF_SETUP, VIE_PROF_FAMILIES
+};
+struct ProfEventPair {
+  cudaEvent_t a, b;
+  int family;
+};
+unsigned long long* prof_bytes(int family);     // device counter, nullptr when off
+int prof_epoch();                               // -1 when off
+int prof_begin(int family, cudaStream_t s);     // handle for prof_end (or -1)
+void prof_end(int handle, cudaStream_t s);
+void prof_set_capture_sink(std::vector<ProfEventPair>* sink);
+void prof_harvest_graph(std::vector<ProfEventPair>& pairs);
+void prof_release_pairs(std::vector<ProfEventPair>& pairs);
+
+// RAII bracket of one launch
+struct ProfScope {
+  int h;
+  cudaStream_t s;
+  ProfScope(int family, cudaStream_t st) : h(prof_begin(family, st)), s(st) {}
+  ~ProfScope() { prof_end(h, s); }
+};
+
 template <typename T> struct LineArgs {
   const cx<T>* in;
   cx<T>* out;
@@ -87,6 +114,9 @@ template <typename T> struct LineArgs {
   long long chi_os, chi_ls, chi_cs;    // chi index = o*chi_os + p*chi_ls + c*chi_cs
   int batch_per_rhs;                   // batches per RHS (3 components) for `active`
   const int* active;                   // per-RHS flag (nullptr = all active)
+  int prof_family;                     // profiler family of this launch
+  unsigned long long* prof;            // profiler byte counter (nullptr = off)
+  unsigned long long prof_batch_bytes; // algorithmic bytes per active batch index
 };
 
 template <typename T> void launch_line_fft(const LineArgs<T>& a, cudaStream_t s);
