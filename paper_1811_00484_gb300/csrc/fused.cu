@@ -12,7 +12,7 @@
 // with signs, for the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2) of every
 // right-hand side.  The stored (uncompressed) variant reads the six spectra
 // from memory instead.
-#include "fft.cuh"
+#include "warpfft.cuh"
 
 namespace vie {
 
@@ -183,6 +183,145 @@ __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
   }
 }
 
+// Register-resident variant for P3 = 32 R: one CTA of four warps per (k1, k2)
+// group, one warp per mirror z-line holding the three components of every
+// right-hand side in registers.  Forward lane FFT, voxel-wise product in the
+// bit-reversed lane layout, inverse lane FFT: no shared-memory round trips
+// and no block barriers after the rebuild.
+template <int R, bool STORED>
+__global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> a) {
+  using C = float2;
+  constexpr int P3 = 32 * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int n3 = a.n3, H3 = a.H3;
+  const int g = blockIdx.x;
+  const int k1 = g / a.H2, k2 = g % a.H2;
+  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
+  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
+  const int nl = nx * ny;
+  if (a.prof != nullptr && blockIdx.x == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
+
+  C* roots = reinterpret_cast<C*>(smem_raw);
+  C* ghalf = roots + P3;               // [6][H3]
+  C* wv = ghalf + 6 * H3;              // [6][r3max]
+  for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
+  if (!STORED) {
+    for (int it = tid; it < 6 * a.r3max; it += nth) {
+      const int c = it / a.r3max, gm = it % a.r3max;
+      const CompMeta<float> m = a.meta[c];
+      C acc = make_float2(0.f, 0.f);
+      if (gm < m.r3) {
+        const C* S = m.slab + (long long)k1 * a.r2max * a.r3max;
+        const C* u2 = m.U2 + (long long)k2 * m.r2;
+        for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max + gm], acc);
+      }
+      wv[it] = acc;
+    }
+    __syncthreads();
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it % H3;
+      const CompMeta<float> m = a.meta[c];
+      const C* u3 = m.U3 + (long long)kk * m.r3;
+      const C* w = wv + c * a.r3max;
+      C acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
+      ghalf[it] = acc;
+    }
+  }
+  __syncthreads();
+  if (warp >= nl) return;                  // no block barrier follows
+
+  const int ix = warp / ny, iy = warp % ny;
+  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
+  const int br = brev5(lane);
+  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
+  for (int b = 0; b < a.B; ++b) {
+    if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
+    C v[3][R];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+      }
+      warp_fft_fwd<C, float, R>(v[comp], lane, roots, P3);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int kk = q + R * br;                       // z-frequency held in register q
+      C gc[6];
+      if (STORED) {
+        const long long off = ((long long)kx * a.P2 + ky) * P3 + kk;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) gc[c] = a.spec[c * a.spec_stride + off];
+      } else {
+        const bool zm = 2 * kk > P3;
+        const int fold = zm ? P3 - kk : kk;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          int s = 1;
+          if (ix) s *= kParity[c][0];
+          if (iy) s *= kParity[c][1];
+          if (zm) s *= kParity[c][2];
+          const C gv = ghalf[c * H3 + fold];
+          gc[c] = (s > 0) ? gv : make_float2(-gv.x, -gv.y);
+        }
+      }
+      const C jx = v[0][q], jy = v[1][q], jz = v[2][q];
+      v[0][q] = gc[0] * jx + gc[1] * jy + gc[2] * jz;
+      v[1][q] = gc[1] * jx + gc[3] * jy + gc[4] * jz;
+      v[2][q] = gc[2] * jx + gc[4] * jy + gc[5] * jz;
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      warp_fft_inv<C, float, R>(v[comp], lane, roots, P3);
+      C* dst = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        if (p < n3) dst[p] = v[comp][j];
+      }
+    }
+  }
+}
+
+template <int R, bool STORED>
+static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
+  const size_t smem = (size_t)(32 * R + 6 * a.H3 + 6 * a.r3max) * sizeof(float2);
+  const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
+  a.prof = prof_bytes(fam);
+  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);
+  a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(float2) : 0ull;
+  ProfScope ps(fam, s);
+  fused_warp_kernel<R, STORED><<<a.H1 * a.H2, 128, smem, s>>>(a);
+}
+
+template <bool STORED>
+static bool launch_fused_warp(const FusedArgs<float>& a, cudaStream_t s) {
+  if (a.P3 % 32 != 0) return false;
+  switch (a.P3 / 32) {
+    case 1: launch_fused_warp_r<1, STORED>(a, s); return true;
+    case 2: launch_fused_warp_r<2, STORED>(a, s); return true;
+    case 3: launch_fused_warp_r<3, STORED>(a, s); return true;
+    case 4: launch_fused_warp_r<4, STORED>(a, s); return true;
+    case 5: launch_fused_warp_r<5, STORED>(a, s); return true;
+    case 6: launch_fused_warp_r<6, STORED>(a, s); return true;
+    case 8: launch_fused_warp_r<8, STORED>(a, s); return true;
+    case 10: launch_fused_warp_r<10, STORED>(a, s); return true;
+    case 12: launch_fused_warp_r<12, STORED>(a, s); return true;
+    case 16: launch_fused_warp_r<16, STORED>(a, s); return true;
+    default: return false;
+  }
+}
+
 template <typename T>
 static size_t fused_smem(const FusedArgs<T>& a, int LR) {
   return (size_t)(a.P3 + 6 * a.H3 + 6 * a.r3max + 2 * LR * 3 * a.ld) * sizeof(cx<T>);
@@ -190,6 +329,9 @@ static size_t fused_smem(const FusedArgs<T>& a, int LR) {
 
 template <typename T, bool STORED>
 static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (launch_fused_warp<STORED>(a, s)) return VIE_OK;
+  }
   const size_t limit = 227 * 1024;
   int LR = 4;
   while (LR > 1 && fused_smem(a, LR) > limit) LR /= 2;

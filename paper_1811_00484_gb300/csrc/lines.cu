@@ -8,7 +8,7 @@
 // (points lin..N-1 read as zero), cropping (only points < lout stored),
 // conjugation, the contrast product and the final scale/subtract of the
 // system operator are fused into the load and store loops.
-#include "fft.cuh"
+#include "warpfft.cuh"
 
 namespace vie {
 
@@ -68,6 +68,119 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
   }
 }
 
+// Register-resident variant for N = 32 R (columns contiguous in memory): the
+// CTA stages a tile of TW columns in shared memory (coalesced rows), each
+// warp pulls whole columns into registers, transforms them with the lane FFT
+// and writes them back, so the tile is touched by two block barriers only.
+// Forward transforms read the tile in natural order and write the
+// bit-reversed lane layout to its natural rows; inverse transforms read the
+// bit-reversed layout from the natural rows.
+template <int R, int TW>
+__global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a) {
+  using C = float2;
+  constexpr int N = 32 * R;
+  constexpr int LD = TW + 1;                 // odd stride: column reads are conflict-free
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = reinterpret_cast<C*>(smem_raw);  // element (row p, column c) at p * LD + c
+  C* roots = tile + N * LD;
+
+  const int c0 = blockIdx.x * TW;
+  const int o = blockIdx.y;
+  const int bb = blockIdx.z;
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0)
+    atomicAdd(a.prof, a.prof_batch_bytes);
+  const int ncols = min(TW, a.ncol - c0);
+
+  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
+  for (int e = tid; e < a.lin * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c < ncols) {
+      C v = in[p * a.in_ls + c];
+      if (a.flags & PRO_CONJ) v = conjg(v);
+      if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      tile[p * LD + c] = v;
+    }
+  }
+  __syncthreads();
+
+  const int br = brev5(lane);
+  for (int c = warp; c < ncols; c += nwarp) {
+    C v[R];
+    if (!a.inverse) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        v[j] = p < a.lin ? tile[p * LD + c] : make_float2(0.f, 0.f);
+      }
+      warp_fft_fwd<C, float, R>(v, lane, roots, N);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const int p = k1 + R * br;
+        if (p < a.lout) tile[p * LD + c] = v[k1];
+      }
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[(k1 + R * br) * LD + c];
+      warp_fft_inv<C, float, R>(v, lane, roots, N);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        if (p < a.lout) tile[p * LD + c] = v[j];
+      }
+    }
+  }
+  __syncthreads();
+
+  const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0;
+  C* out = a.out + obase;
+  for (int e = tid; e < a.lout * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c >= ncols) continue;
+    C v = a.scale * tile[p * LD + c];
+    if (a.flags & EPI_CONJ) v = conjg(v);
+    const long long oi = p * a.out_ls + c;
+    if (a.flags & (EPI_SUB | EPI_ADD)) {
+      if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      const C w = a.addend[obase + oi];
+      v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
+    }
+    out[oi] = v;
+  }
+}
+
+template <int R>
+static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
+  constexpr int TW = 16;
+  const size_t smem = (size_t)(32 * R * (TW + 1) + 32 * R) * sizeof(float2);
+  dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
+  line_warp_kernel<R, TW><<<grid, 256, smem, s>>>(a);
+}
+
+static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
+  const int N = a.plan.N;
+  if (N % 32 != 0 || a.in_cs != 1 || a.out_cs != 1) return false;
+  if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
+  switch (N / 32) {
+    case 1: launch_warp_r<1>(a, s); return true;
+    case 2: launch_warp_r<2>(a, s); return true;
+    case 3: launch_warp_r<3>(a, s); return true;
+    case 4: launch_warp_r<4>(a, s); return true;
+    case 5: launch_warp_r<5>(a, s); return true;
+    case 6: launch_warp_r<6>(a, s); return true;
+    case 8: launch_warp_r<8>(a, s); return true;
+    case 10: launch_warp_r<10>(a, s); return true;
+    case 12: launch_warp_r<12>(a, s); return true;
+    case 16: launch_warp_r<16>(a, s); return true;
+    default: return false;
+  }
+}
+
 template <typename T, int TW>
 static void launch_tw(LineArgs<T> a, size_t smem, cudaStream_t s) {
   dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
@@ -80,6 +193,9 @@ static void launch_tw(LineArgs<T> a, size_t smem, cudaStream_t s) {
 // ping-pong buffers and root table fit in 227 KB of shared memory.
 template <typename T>
 void launch_line_fft(const LineArgs<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (launch_warp(a, s)) return;
+  }
   const int N = a.plan.N;
   auto bytes = [&](int tw) { return (size_t)(2 * N * tw + N) * sizeof(cx<T>); };
   const size_t limit = 227 * 1024;
@@ -112,6 +228,10 @@ int line_fft_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "line kernel attributes");
 }
 

@@ -75,7 +75,10 @@ int prof_begin(int family, cudaStream_t s) {
   Pair q = p.pool.back();
   p.pool.pop_back();
   q.family = family;
-  cudaEventRecord(q.a, s);
+  // inside a stream capture the record becomes an event node that is visible
+  // outside the graph only with cudaEventRecordExternal
+  if (t_capture_sink) cudaEventRecordWithFlags(q.a, s, cudaEventRecordExternal);
+  else cudaEventRecord(q.a, s);
   std::vector<Pair>& dst = t_capture_sink ? *t_capture_sink : p.pending;
   dst.push_back(q);
   return (int)dst.size() - 1;
@@ -86,7 +89,10 @@ void prof_end(int handle, cudaStream_t s) {
   Profiler& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   std::vector<Pair>& dst = t_capture_sink ? *t_capture_sink : p.pending;
-  if (handle < (int)dst.size()) cudaEventRecord(dst[handle].b, s);
+  if (handle < (int)dst.size()) {
+    if (t_capture_sink) cudaEventRecordWithFlags(dst[handle].b, s, cudaEventRecordExternal);
+    else cudaEventRecord(dst[handle].b, s);
+  }
 }
 
 void prof_set_capture_sink(std::vector<ProfEventPair>* sink) {
