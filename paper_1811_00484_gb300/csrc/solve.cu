@@ -34,9 +34,20 @@ __device__ __forceinline__ double2 wsum(double2 v) {
 }
 
 // partial[b][i][chunk] = sum over the chunk of conj(V_i[b]) w[b], i = 0..k.
-// Each thread forms its kPer products in FP32 (the data are FP32); the sums
-// across threads, warps and chunks are FP64 (GB300's FP64 rate is far below
-// its FP32 rate, so FP64 is kept out of the per-element work).
+// Eight basis vectors are read per step (their loads are all in flight at
+// once), each thread forms its kPer products in FP32 (the data are FP32) and
+// the warp sums them in FP32; sums across warps and chunks are FP64 (GB300's
+// FP64 rate is far below its FP32 rate, so FP64 stays out of per-element work).
+constexpr int kDotBlock = 8;
+
+__device__ __forceinline__ float2 wsum32(float2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict__ V,
                                                         const float2* __restrict__ w, int k, int B,
                                                         long long N, int nchunk, double2* partial,
@@ -48,26 +59,35 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict
   __shared__ double2 red[kThreads / 32][129];
   const long long base = (long long)chunk * kChunk;
   float2 wv[kPer];
+  long long idxs[kPer];
 #pragma unroll
   for (int e = 0; e < kPer; ++e) {
     const long long idx = base + e * kThreads + threadIdx.x;
-    wv[e] = idx < N ? w[(long long)b * N + idx] : make_float2(0.f, 0.f);
+    const bool in = idx < N;
+    idxs[e] = in ? idx : 0;                      // loads stay in bounds; the product is zeroed
+    wv[e] = in ? w[(long long)b * N + idx] : make_float2(0.f, 0.f);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = 0; i <= k; ++i) {
-    const float2* vi = V + ((long long)i * B + b) * N;
-    float ax = 0.f, ay = 0.f;
+  for (int i0 = 0; i0 <= k; i0 += kDotBlock) {
+    float2 acc[kDotBlock];
 #pragma unroll
-    for (int e = 0; e < kPer; ++e) {
-      const long long idx = base + e * kThreads + threadIdx.x;
-      if (idx < N) {
-        const float2 v = vi[idx];
+    for (int u = 0; u < kDotBlock; ++u) {
+      const int i = min(i0 + u, k);              // repeats vector k past the end; not stored
+      const float2* vi = V + ((long long)i * B + b) * N;
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        const float2 v = vi[idxs[e]];
         ax = fmaf(v.x, wv[e].x, fmaf(v.y, wv[e].y, ax));
         ay = fmaf(v.x, wv[e].y, fmaf(-v.y, wv[e].x, ay));
       }
+      acc[u] = make_float2(ax, ay);
     }
-    double2 acc = wsum(make_double2((double)ax, (double)ay));
-    if (lane == 0) red[warp][i] = acc;
+#pragma unroll
+    for (int u = 0; u < kDotBlock; ++u) {
+      const float2 t = wsum32(acc[u]);
+      if (lane == 0 && i0 + u <= k) red[warp][i0 + u] = make_double2((double)t.x, (double)t.y);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= k; i += kThreads) {
@@ -175,46 +195,81 @@ __global__ void __launch_bounds__(kThreads) norm32_kernel(const float2* v, long 
   }
 }
 
-// One Givens step per RHS: finish column k (h_{k+1,k} = nrm), rotate, test convergence,
-// and store 1/h_{k+1,k} for the normalisation of the next basis vector.
-__global__ void givens_kernel(double2* H, double2* cs, double2* sn, double2* g, const double* nrm,
-                              double* inv, int k, int m, int B, int* active, int* iters,
-                              const double* tol_abs, int* count) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B || !active[b]) return;
-  count[b] += 1;
+// One Givens step per RHS (one warp each): finish column k (h_{k+1,k} = nrm),
+// apply the k earlier rotations, form the new one, update g, test convergence
+// and store 1/h_{k+1,k} for the normalisation of the next basis vector.  The
+// column and the rotations are staged in shared memory so the sequential
+// rotation chain does not wait on global memory.
+__global__ void __launch_bounds__(128) givens_kernel(double2* H, double2* cs, double2* sn, double2* g,
+                                                     const double* nrm, double* inv, int k, int m,
+                                                     int B, int* active, int* iters,
+                                                     const double* tol_abs, int* count) {
+  __shared__ double2 sh[4][130], sc[4][128], ss[4][128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * 4 + warp;
+  if (b >= B || !active[b]) return;            // warp-uniform; no block barrier below
   double2* h = H + ((long long)b * m + k) * (m + 1);
-  const double hk1 = nrm[b];
-  h[k + 1] = make_double2(hk1, 0.0);
   double2* c = cs + (long long)b * m;
   double2* s = sn + (long long)b * m;
-  for (int i = 0; i < k; ++i) {
-    const double2 t = c[i] * h[i] + s[i] * h[i + 1];
-    h[i + 1] = (-1.0) * (conjg(s[i]) * h[i]) + conjg(c[i]) * h[i + 1];
-    h[i] = t;
+  for (int i = lane; i <= k; i += 32) sh[warp][i] = h[i];
+  for (int i = lane; i < k; i += 32) {
+    sc[warp][i] = c[i];
+    ss[warp][i] = s[i];
   }
-  const double2 a = h[k], bb = h[k + 1];
-  const double den = sqrt(abs2(a) + abs2(bb));
-  double2 ck, sk;
-  if (den == 0.0) {
-    ck = make_double2(1.0, 0.0);
-    sk = make_double2(0.0, 0.0);
-  } else {
-    ck = (1.0 / den) * conjg(a);
-    sk = (1.0 / den) * conjg(bb);
+  __syncwarp();
+  if (lane == 0) {
+    count[b] += 1;
+    double2* hh = sh[warp];
+    const double hk1 = nrm[b];
+    hh[k + 1] = make_double2(hk1, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double2 ci = sc[warp][i], si = ss[warp][i];
+      const double2 t = ci * hh[i] + si * hh[i + 1];
+      hh[i + 1] = (-1.0) * (conjg(si) * hh[i]) + conjg(ci) * hh[i + 1];
+      hh[i] = t;
+    }
+    const double2 a = hh[k], bb = hh[k + 1];
+    const double den = sqrt(abs2(a) + abs2(bb));
+    double2 ck, sk;
+    if (den == 0.0) {
+      ck = make_double2(1.0, 0.0);
+      sk = make_double2(0.0, 0.0);
+    } else {
+      ck = (1.0 / den) * conjg(a);
+      sk = (1.0 / den) * conjg(bb);
+    }
+    c[k] = ck;
+    s[k] = sk;
+    hh[k] = ck * a + sk * bb;
+    hh[k + 1] = make_double2(0.0, 0.0);
+    double2* gb = g + (long long)b * (m + 1);
+    const double2 gk = gb[k];
+    gb[k + 1] = (-1.0) * (conjg(sk) * gk);
+    gb[k] = ck * gk;
+    iters[b] = k + 1;
+    const double res = sqrt(abs2(gb[k + 1]));
+    const bool breakdown = !(hk1 > 1e-300) || !(sqrt(abs2(hh[k])) > 0.0);
+    if (res <= tol_abs[b] || breakdown || k + 1 == m || !(res == res)) active[b] = 0;
+    inv[b] = hk1 > 1e-300 ? 1.0 / hk1 : 0.0;
   }
-  c[k] = ck;
-  s[k] = sk;
-  h[k] = ck * a + sk * bb;
-  h[k + 1] = make_double2(0.0, 0.0);
-  double2* gb = g + (long long)b * (m + 1);
-  gb[k + 1] = (-1.0) * (conjg(sk) * gb[k]);
-  gb[k] = ck * gb[k];
-  iters[b] = k + 1;
-  const double res = sqrt(abs2(gb[k + 1]));
-  const bool breakdown = !(hk1 > 1e-300) || !(sqrt(abs2(h[k])) > 0.0);
-  if (res <= tol_abs[b] || breakdown || k + 1 == m || !(res == res)) active[b] = 0;
-  inv[b] = hk1 > 1e-300 ? 1.0 / hk1 : 0.0;
+  __syncwarp();
+  for (int i = lane; i <= k + 1; i += 32) h[i] = sh[warp][i];
+}
+
+// DGKS test after the first Gram-Schmidt pass: re-orthogonalise only when the
+// projection removed most of w, ||w'||^2 < (1/2) (||w'||^2 + ||h||^2).
+__global__ void dgks_kernel(const double2* coef, const double* nrm, int k, int B, const int* active,
+                            int* again) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int r = 0;
+  if (active[b]) {
+    double hh = 0.0;
+    for (int i = 0; i <= k; ++i) hh += abs2(coef[(long long)b * 129 + i]);
+    const double w2 = nrm[b] * nrm[b];
+    r = (w2 < 0.5 * (w2 + hh)) ? 1 : 0;
+  }
+  again[b] = r;
 }
 
 // V_{k+1}[b] = w[b] * inv[b]  (only for RHS still active after the Givens step)
@@ -455,7 +510,7 @@ struct SolverState {
   float2 *V, *W, *d, *r32;
   double2 *H, *cs, *sn, *g, *coef, *partial;
   double *nrm_partial, *nrm, *inv, *beta, *tol_abs, *rnorm, *bnorm, *pb;
-  int *active, *iters, *want, *count_it, *count_mv;
+  int *active, *iters, *want, *count_it, *count_mv, *again;
   double2 *x, *b64, *r64, *ax64;
   float2* chi32;
   double2* chi64;
@@ -520,7 +575,7 @@ static size_t carve_bytes(int B, int m, long long N, int nchunk) {
   carve<double>(p, (size_t)B * nchunk);               // norm partials
   for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm inv beta tol_abs rnorm bnorm
   carve<double>(p, (size_t)B * nchunk);               // pb
-  for (int i = 0; i < 5; ++i) carve<int>(p, B);       // active iters want counters
+  for (int i = 0; i < 6; ++i) carve<int>(p, B);       // active iters want counters again
   for (int i = 0; i < 4; ++i) carve<double2>(p, (size_t)B * N);   // x b64 r64 ax64
   carve<float2>(p, (size_t)N / 3);                    // chi32
   carve<double2>(p, (size_t)N / 3);                   // chi64
@@ -582,6 +637,7 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->want = carve<int>(p, B);
   st->count_it = carve<int>(p, B);
   st->count_mv = carve<int>(p, B);
+  st->again = carve<int>(p, B);
   st->x = carve<double2>(p, (size_t)B * N);
   st->b64 = carve<double2>(p, (size_t)B * N);
   st->r64 = carve<double2>(p, (size_t)B * N);
@@ -610,29 +666,35 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   dim3 grid(nc, B);
   const int rblocks = (k + 1 + 7) / 8;
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
+  // classical Gram-Schmidt; a second pass only where the DGKS test asks for it
   for (int pass = 0; pass < 2; ++pass) {
+    const int* mask = pass == 0 ? st->active : st->again;
     {
       ProfScope ps(PF_DOTS, s);
-      dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, st->active,
+      dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, mask,
                                             prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
       reduce_dots_kernel<<<dim3(rblocks, B), 256, 0, s>>>(st->partial, k, nc, st->coef, st->H, m,
-                                                          pass, st->active);
+                                                          pass, mask);
     }
     {
       ProfScope ps(PF_UPDATE, s);
-      update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc,
-                                              pass == 1 ? st->nrm_partial : nullptr, st->active,
+      update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc, st->nrm_partial, mask,
                                               prof_bytes(PF_UPDATE), (k + 3) * vec);
+    }
+    {
+      ProfScope ps(PF_SMALL, s);
+      reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, mask);
+      if (pass == 0)
+        dgks_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->coef, st->nrm, k, B, st->active, st->again);
     }
   }
   {
     ProfScope ps(PF_SMALL, s);
-    reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, st->active);
-    givens_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m,
-                                               B, st->active, st->iters, st->tol_abs, st->count_it);
+    givens_kernel<<<(B + 3) / 4, 128, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m,
+                                              B, st->active, st->iters, st->tol_abs, st->count_it);
     scale_into_kernel<<<grid, kThreads, 0, s>>>(w, st->V + (long long)(k + 1) * B * N, st->inv, N,
                                                 st->active);
   }
