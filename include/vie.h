@@ -233,8 +233,11 @@ int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* ou
 
 /*
  * Benchmark instrumentation (no counterpart in the paper).  Between
- * vie_profile_start() and vie_profile_stop() every launch of the library's
- * kernel families is bracketed by CUDA events on the stream it runs on
+ * vie_profile_start(mask) and vie_profile_stop() every launch of the kernel
+ * families selected by `mask` (bit f = family f in the order line_x, line_y,
+ * fused_tucker, fused_stored, line_iy, line_ix, slab_cores, arnoldi_dots,
+ * arnoldi_update, arnoldi_small, fp64_vector, setup; ~0u = all) is
+ * bracketed by CUDA events on the stream it runs on
  * (inside CUDA graphs as event nodes read after each replay), and kernels
  * add the algorithmic bytes they move for active right-hand sides to a
  * per-family device counter.  vie_profile_stop() synchronises the device
@@ -249,7 +252,7 @@ typedef struct vie_profile_entry {
     double bytes;
 } vie_profile_entry;
 
-int vie_profile_start(void);
+int vie_profile_start(unsigned mask);
 int vie_profile_stop(vie_profile_entry* out, int max_entries, int* count);
 
 /* Release `op` and everything it owns (NULL is allowed). */

@@ -96,7 +96,7 @@ def _load():
         "vie_contrast_gradient": [vp, vp, vp, vp, ci, cd, ci, vp],
         "vie_incident_dipole": [vp, pd, ci, vp, ci, vp],
         "vie_destroy": [vp],
-        "vie_profile_start": [],
+        "vie_profile_start": [ctypes.c_uint],
         "vie_profile_stop": [ctypes.POINTER(ProfileEntry), ci, ctypes.POINTER(ci)],
         "vie_status_string": [ci],
         "vie_last_error": [],
@@ -302,9 +302,16 @@ class Operator:
         return out
 
 
-def profile_start():
-    """Start per-kernel-family event timing (vie_profile_start)."""
-    _check(lib.vie_profile_start(), "vie_profile_start")
+PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy", "line_ix",
+                    "slab_cores", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
+                    "setup")
+
+
+def profile_start(families=None):
+    """Start per-kernel-family event timing (vie_profile_start); None = every family."""
+    mask = 0xFFFFFFFF if families is None else \
+        sum(1 << PROFILE_FAMILIES.index(f) for f in families)
+    _check(lib.vie_profile_start(ctypes.c_uint(mask)), "vie_profile_start")
 
 
 def profile_stop():

@@ -18,6 +18,7 @@ struct Pair {
 struct Profiler {
   std::mutex mu;
   bool on = false;
+  unsigned mask = 0;
   int epoch = 0;
   std::vector<Pair> pool;
   std::vector<Pair> pending;                 // direct launches since the last harvest
@@ -62,7 +63,7 @@ int prof_epoch() { return prof().on ? prof().epoch : -1; }
 
 int prof_begin(int family, cudaStream_t s) {
   Profiler& p = prof();
-  if (!p.on) return -1;
+  if (!p.on || !(p.mask & (1u << family))) return -1;
   std::lock_guard<std::mutex> lk(p.mu);
   if (p.pool.empty()) {
     Pair q;
@@ -118,8 +119,9 @@ static_assert(sizeof(Pair) == sizeof(ProfEventPair), "event pair layout");
 
 extern "C" {
 
-int vie_profile_start(void) {
+int vie_profile_start(unsigned mask) {
   Profiler& p = prof();
+  p.mask = mask;
   std::lock_guard<std::mutex> lk(p.mu);
   if (!p.d_bytes) {
     cudaError_t e = cudaMalloc(&p.d_bytes, VIE_PROF_FAMILIES * sizeof(unsigned long long));
