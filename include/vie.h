@@ -179,6 +179,29 @@ int vie_reserve(vie_op* op, int max_batch);
 int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
                int precision, void* stream);
 
+/*
+ * Y = G J like vie_matvec with path VIE_PATH_TUCKER and precision VIE_C64,
+ * but without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they need a product, for example code being captured into a CUDA graph
+ * (cudaMalloc is not allowed during capture), serving loops whose device
+ * memory is owned by another allocator under a fixed budget, or callbacks
+ * that must not trigger the device-wide synchronisation cudaMalloc and
+ * cudaFree can cause.
+ * Its scratch is one fixed 64 MiB array compiled into the library (every
+ * GPU that loads the library holds it until the process exits).  A call
+ * needs 24 B (P1 n2 n3 + P1 P2 n3) bytes of it; larger grids or batches
+ * are rejected with VIE_ERR_ARG (use vie_matvec).  Nothing in the scratch
+ * needs to start at zero: every call overwrites what it reads.
+ * The first call on each device looks up the scratch address (with that
+ * device current); make that first call before any stream capture.
+ * All calls share the one array, and the operator's slab-core buffer, so
+ * calls that overlap on the GPU (different streams, or concurrent host
+ * threads) race; serialise them.  J, Y: device [B][3][n1][n2][n3] c64.
+ */
+int vie_matvec_noalloc(const vie_op* op, const void* J, void* Y, int B,
+                       void* stream);
+
 /* X = G^H Y = conj(G conj(Y)) (G is complex symmetric).  Layout as vie_matvec. */
 int vie_matvec_adjoint(const vie_op* op, const void* Y, void* X, int B,
                        int path, int precision, void* stream);

@@ -36,7 +36,7 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_reserve", "vie_matvec", "vie_matvec_adjoint", "vie_apply_system",
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
-           "vie_profile_stop")
+           "vie_profile_stop", "vie_matvec_noalloc")
 
 
 class VieError(RuntimeError):
@@ -89,6 +89,7 @@ def _load():
         "vie_reserve": [vp, ci],
         "vie_matvec": [vp, vp, vp, ci, ci, ci, vp],
         "vie_matvec_adjoint": [vp, vp, vp, ci, ci, ci, vp],
+        "vie_matvec_noalloc": [vp, vp, vp, ci, vp],
         "vie_apply_system": [vp, vp, vp, vp, ci, ci, ci, ci, vp],
         "vie_total_field": [vp, vp, vp, vp, ci, ci, ci, vp],
         "vie_solve": [vp, vp, vp, vp, ci, ci, ci, ctypes.POINTER(SolveOpts),

@@ -46,18 +46,16 @@ int ensure_workspace(vie_op* op, int B) {
   return VIE_OK;
 }
 
+// The stages of one matvec with the caller-chosen scratch `ws` (T1 then T2).
 template <typename T>
-int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
-                int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
-                cudaStream_t s) {
+int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
+               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
+               const int* active, cudaStream_t s) {
   using C = cx<T>;
-  if (workspace_bytes_for(op, B) > op->ws.bytes) {
-    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
-  }
   const bool stored = (path == VIE_PATH_UNCOMPRESSED);
   const long long n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
   const long long P1 = op->P[0], P2 = op->P[1], P3 = op->P[2];
-  C* T1 = static_cast<C*>(op->ws.ptr);
+  C* T1 = static_cast<C*>(ws);
   C* T2 = T1 + (size_t)B * 3 * P1 * n2 * n3;
   const C* r[3];
   for (int q = 0; q < 3; ++q) {
@@ -170,6 +168,19 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
   return VIE_OK;
 }
 
+template <typename T>
+int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
+                int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
+                cudaStream_t s) {
+  if (workspace_bytes_for(op, B) > op->ws.bytes) {
+    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
+  }
+  return matvec_run<T>(op, op->ws.ptr, in, out, B, path, pro_flags, epi_flags, chi, addend, active,
+                       s);
+}
+
+template int matvec_run<float>(const vie_op*, void*, const float2*, float2*, int, int, int, int,
+                               const float2*, const float2*, const int*, cudaStream_t);
 template int matvec_impl<float>(const vie_op*, const float2*, float2*, int, int, int, int,
                                 const float2*, const float2*, const int*, cudaStream_t);
 template int matvec_impl<double>(const vie_op*, const double2*, double2*, int, int, int, int,

@@ -196,6 +196,11 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
                 cudaStream_t s);
 int ensure_workspace(vie_op* op, int B);
+// the same stages with an explicit scratch buffer of at least matvec_scratch_bytes() bytes
+template <typename T>
+int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
+               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
+               const int* active, cudaStream_t s);
 size_t workspace_bytes_for(const vie_op* op, int B);
 
 // setup internals (setup.cu)
