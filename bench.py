@@ -38,8 +38,12 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="solve", choices=["solve", "matvec"],
-                   help="matvec: only K timed batched matvecs (a small command for profilers)")
+    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1"],
+                   help="matvec: only K timed batched matvecs; solve1: K solves only "
+                        "(small commands for profilers)")
+    p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
+    p.add_argument("--orth", type=int, default=2, choices=[1, 2],
+                   help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
     return p.parse_args()
@@ -162,6 +166,35 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_solve1_mode(args):
+    """K solves of the bench workload and nothing else (for ncu captures)."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    wl = workloads.solve_n64() if args.n == 64 else workloads.make("custom", args.n, 1, incident="plane")
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed")
+    chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
+    einc = torch.from_numpy(wl.einc.astype(np.complex64)).cuda()
+    kw = dict(tol=1e-6, restart=50, path=args.path, use_graph=not args.no_graph, orth=args.orth)
+    for _ in range(args.warmup):
+        op.solve(chi, einc, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_solve")
+    infos = [op.solve(chi, einc, **kw)[1] for _ in range(args.steps)]
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    print(json.dumps({"mode": "solve1", "n": args.n, "path": args.path, "graph": not args.no_graph,
+                      "orth": args.orth, "ms_per_solve": 1e3 * el / args.steps,
+                      "iterations": infos[-1]["iterations"], "refine_steps": infos[-1]["refine_steps"],
+                      "relres": infos[-1]["relres"],
+                      "matvecs_per_s": sum(i["matvecs"] for i in infos) / el}))
+
+
 def run_matvec_mode(args):
     """K batched matvecs of the bench workload, nothing else (for ncu captures)."""
     import numpy as np
@@ -199,6 +232,8 @@ def main():
         return run_reference(args)
     if args.mode == "matvec":
         return run_matvec_mode(args)
+    if args.mode == "solve1":
+        return run_solve1_mode(args)
     import numpy as np
     import torch
 
@@ -219,7 +254,7 @@ def main():
     chi_h = torch.from_numpy(wl.chi.astype(np.complex64)).pin_memory()
     einc_h = torch.from_numpy(wl.einc.astype(np.complex64)).pin_memory()
     w_h = torch.empty_like(einc_h).pin_memory()
-    solve_kw = dict(tol=1e-6, restart=50, max_outer=200, max_refine=20)
+    solve_kw = dict(tol=1e-6, restart=50, max_outer=200, max_refine=20, orth=args.orth)
 
     def barrier():
         if world > 1:

@@ -119,6 +119,10 @@ typedef struct vie_solve_opts {
     int path;            /* VIE_PATH_TUCKER or VIE_PATH_UNCOMPRESSED            */
     int use_graph;       /* replay each restart cycle as a CUDA graph         */
     int refine;          /* 1: FP64 iterative refinement; 0: FP32 GMRES only  */
+    int orth;            /* Arnoldi: 2 = classical Gram-Schmidt with a second
+                            pass when the DGKS test asks (||w'|| < ||w||/sqrt2),
+                            1 = one classical pass (the FP64 refinement
+                            absorbs the orthogonality loss)                   */
 } vie_solve_opts;
 
 typedef struct vie_solve_info {

@@ -60,7 +60,7 @@ class OpInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int), ("path", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("refine", ctypes.c_int), ("orth", ctypes.c_int)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -257,7 +257,7 @@ class Operator:
 
     def solve(self, chi, rhs, incident=True, adjoint=False, x0=None, tol=1e-6, restart=50,
               max_outer=200, inner_tol=None, max_refine=20, path="tucker", use_graph=True,
-              refine=True, out=None, raise_on_failure=True):
+              refine=True, orth=2, out=None, raise_on_failure=True):
         """Solve A w = b (or A^H w = b); b = chi * rhs when ``incident``.  Returns (w, info)."""
         B = _batch(rhs, self.n)
         w = self._out(rhs, out)
@@ -268,7 +268,8 @@ class Operator:
         if inner_tol is None:
             inner_tol = max(tol, 1e-5) if refine else tol
         opts = SolveOpts(float(tol), int(restart), int(max_outer), float(inner_tol),
-                         int(max_refine), PATHS[path], int(bool(use_graph)), int(bool(refine)))
+                         int(max_refine), PATHS[path], int(bool(use_graph)), int(bool(refine)),
+                         int(orth))
         inf = SolveInfo()
         st = lib.vie_solve(self._h, _dev(chi, "chi", self.n), _dev(rhs, "rhs", self.n),
                            _dev(w, "w", self.n), B, flags, _precision(rhs), ctypes.byref(opts),

@@ -267,7 +267,8 @@ int vie_solve(const vie_op* op, const void* chi, const void* rhs, void* w, int B
     return VIE_ERR_ARG;
   }
   if (opts->restart < 1 || opts->restart > 128 || opts->max_outer < 1 || opts->max_refine < 0 ||
-      opts->max_refine > 64 || !(opts->tol > 0.0) || !(opts->inner_tol > 0.0)) {
+      opts->max_refine > 64 || !(opts->tol > 0.0) || !(opts->inner_tol > 0.0) ||
+      (opts->orth != 1 && opts->orth != 2)) {
     set_error("invalid solve options");
     return VIE_ERR_ARG;
   }

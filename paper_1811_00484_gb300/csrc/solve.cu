@@ -525,6 +525,7 @@ struct SolverState {
   cudaStream_t graph_stream = nullptr;
   int graph_adjoint = -1;
   int graph_prof = -1;                        // profiler epoch the graph was captured in
+  int graph_passes = -1;                      // Gram-Schmidt passes baked into the graph
   std::vector<ProfEventPair> graph_events;    // event nodes of the captured graph
   bool graph_pending = false;                 // a replay ran since the last harvest
 };
@@ -652,7 +653,7 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
 
 // One Arnoldi step k (CGS2) for all active RHS.
 static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, int k, int path,
-                        int adjoint, cudaStream_t s) {
+                        int adjoint, int passes, cudaStream_t s) {
   const int B = st->B, m = st->m, nc = st->nchunk;
   const long long N = st->N;
   const float2* vk = st->V + (long long)k * B * N;
@@ -667,7 +668,7 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   const int rblocks = (k + 1 + 7) / 8;
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
   // classical Gram-Schmidt; a second pass only where the DGKS test asks for it
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     const int* mask = pass == 0 ? st->active : st->again;
     {
       ProfScope ps(PF_DOTS, s);
@@ -687,7 +688,7 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
     {
       ProfScope ps(PF_SMALL, s);
       reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, mask);
-      if (pass == 0)
+      if (pass == 0 && passes > 1)
         dgks_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->coef, st->nrm, k, B, st->active, st->again);
     }
   }
@@ -735,15 +736,15 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
 }
 
 static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int path, int adjoint,
-                     bool use_graph, cudaStream_t s) {
+                     int passes, bool use_graph, cudaStream_t s) {
   if (!use_graph) {
-    for (int k = 0; k < st->m; ++k) VIE_TRY(arnoldi_step(op, st, chi, k, path, adjoint, s));
+    for (int k = 0; k < st->m; ++k) VIE_TRY(arnoldi_step(op, st, chi, k, path, adjoint, passes, s));
     return cycle_tail(op, st, chi, path, adjoint, s);
   }
   // the graph bakes in every pointer it touches: rebuild it when any changes
   if (st->exec && (st->graph_chi != chi || st->graph_stream != s || st->path != path ||
                    st->graph_adjoint != adjoint || st->graph_ws != op->ws.ptr ||
-                   st->graph_prof != prof_epoch())) {
+                   st->graph_prof != prof_epoch() || st->graph_passes != passes)) {
     drop_graph(st);
   }
   if (!st->exec) {
@@ -751,7 +752,8 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
     VIE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     prof_set_capture_sink(&st->graph_events);
     int rc = VIE_OK;
-    for (int k = 0; k < st->m && rc == VIE_OK; ++k) rc = arnoldi_step(op, st, chi, k, path, adjoint, s);
+    for (int k = 0; k < st->m && rc == VIE_OK; ++k)
+      rc = arnoldi_step(op, st, chi, k, path, adjoint, passes, s);
     if (rc == VIE_OK) rc = cycle_tail(op, st, chi, path, adjoint, s);
     prof_set_capture_sink(nullptr);
     cudaError_t e = cudaStreamEndCapture(s, &graph);
@@ -772,6 +774,7 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
     st->graph_adjoint = adjoint;
     st->graph_ws = op->ws.ptr;
     st->graph_prof = prof_epoch();
+    st->graph_passes = passes;
   }
   VIE_CUDA(cudaGraphLaunch(st->exec, s));
   st->graph_pending = true;
@@ -786,7 +789,8 @@ static void harvest_graph(SolverState* st) {
 
 // FP32 GMRES on r32 (unit-norm rows) to relative tolerance `tol` for the RHS in `want`.
 static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint, double tol,
-                       int max_outer, bool use_graph, const std::vector<int>& want, cudaStream_t s) {
+                       int max_outer, int passes, bool use_graph, const std::vector<int>& want,
+                       cudaStream_t s) {
   const int B = st->B, nc = st->nchunk;
   const long long N = st->N;
   dim3 grid(nc, B);
@@ -808,7 +812,7 @@ static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint,
     int nact = 0;
     for (int b = 0; b < B; ++b) nact += act[b];
     if (nact == 0) return VIE_OK;
-    VIE_TRY(run_cycle(op, st, st->chi32, path, adjoint, use_graph, s));
+    VIE_TRY(run_cycle(op, st, st->chi32, path, adjoint, passes, use_graph, s));
   }
   VIE_CUDA(cudaStreamSynchronize(s));
   harvest_graph(st);
@@ -929,7 +933,8 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
     // (with a factor 4 of headroom), never tighter than inner_tol or FP32 allows
     const double need = 0.25 * o->tol / std::max(worst, 1e-300);
     const double itol = o->refine ? std::min(0.5, std::max({o->inner_tol, need, 1e-7})) : o->tol;
-    VIE_TRY(inner_gmres(op, st, path, adjoint, itol, o->max_outer, o->use_graph != 0, want, s));
+    VIE_TRY(inner_gmres(op, st, path, adjoint, itol, o->max_outer, o->orth == 1 ? 1 : 2,
+                        o->use_graph != 0, want, s));
     {
       ProfScope ps(PF_FP64, s);
       accumulate_kernel<<<grid, kThreads, 0, s>>>(st->x, st->d, st->rnorm, N, st->want);

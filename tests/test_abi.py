@@ -62,5 +62,5 @@ def test_struct_layouts_match_header():
     """ctypes mirrors of the header structs have the C sizes."""
     vie = pytest.importorskip("paper_1811_00484_gb300")
     assert ctypes.sizeof(vie.Grid) == 3 * 4 + 4 + 2 * 8
-    assert ctypes.sizeof(vie.SolveOpts) == 8 + 4 + 4 + 8 + 4 * 4
+    assert ctypes.sizeof(vie.SolveOpts) == 8 + 4 + 4 + 8 + 5 * 4 + 4   # trailing pad to 8
     assert ctypes.sizeof(vie.SolveInfo) == 4 * 4 + 8 + 65 * 8
