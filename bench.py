@@ -42,7 +42,7 @@ def parse():
                    help="matvec: only K timed batched matvecs; solve1: K solves only "
                         "(small commands for profilers)")
     p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
-    p.add_argument("--orth", type=int, default=2, choices=[1, 2],
+    p.add_argument("--orth", type=int, default=1, choices=[1, 2],
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])

@@ -257,7 +257,7 @@ class Operator:
 
     def solve(self, chi, rhs, incident=True, adjoint=False, x0=None, tol=1e-6, restart=50,
               max_outer=200, inner_tol=None, max_refine=20, path="tucker", use_graph=True,
-              refine=True, orth=2, out=None, raise_on_failure=True):
+              refine=True, orth=1, out=None, raise_on_failure=True):
         """Solve A w = b (or A^H w = b); b = chi * rhs when ``incident``.  Returns (w, info)."""
         B = _batch(rhs, self.n)
         w = self._out(rhs, out)

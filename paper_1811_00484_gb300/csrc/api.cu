@@ -41,6 +41,26 @@ int component_parity(int c, int axis) {
   return ((a == axis) + (b == axis)) % 2 ? -1 : 1;
 }
 
+int persistent_grid(const void* kernel, int threads, size_t smem, long long work) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long long g = (long long)per_sm * sms;
+  return (int)(work < g ? (work > 0 ? work : 1) : g);
+}
+
 int check_grid(const vie_grid* g) {
   if (!g) { set_error("grid is NULL"); return VIE_ERR_ARG; }
   const int n[3] = {g->n1, g->n2, g->n3};

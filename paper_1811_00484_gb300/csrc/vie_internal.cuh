@@ -209,6 +209,9 @@ int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, c
 int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s);
 int op_tables(vie_op* op);   // FFT plans and root tables of op->P
 int line_fft_init_attributes();
+// persistent grid size for `kernel` with `threads` threads and `smem` bytes of
+// dynamic shared memory: resident CTAs per SM x SMs, capped by `work`
+int persistent_grid(const void* kernel, int threads, size_t smem, long long work);
 int fused_init_attributes();
 
 // solver (solve.cu)

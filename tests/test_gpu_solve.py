@@ -97,6 +97,14 @@ def test_graph_and_direct_launches_agree():
     assert torch.equal(w1, w2)
 
 
+def test_two_pass_gram_schmidt_solve():
+    """orth=2: classical Gram-Schmidt with the DGKS-conditional second pass."""
+    wl, T, Ghat, Gt, op = case((8, 6, 10), tol_svd=1e-8, seed=3)
+    w, info = op.solve(dev(wl.chi, C128), dev(wl.einc, C128), tol=1e-10, orth=2)
+    assert info["converged"]
+    assert residual(Gt, wl.chi, wl.einc, host(w)) <= 2e-10
+
+
 def test_fp32_only_solve():
     wl, T, Ghat, Gt, op = case((8, 6, 10), tol_svd=1e-8, seed=3)
     w, info = op.solve(dev(wl.chi), dev(wl.einc), tol=1e-5, refine=False)
