@@ -83,77 +83,72 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);  // element (row p, column c) at p * LD + c
   C* roots = tile + N * LD;
+
+  const int c0 = blockIdx.x * TW;
+  const int o = blockIdx.y;
+  const int bb = blockIdx.z;
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  const int br = brev5(lane);
+  if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0)
+    atomicAdd(a.prof, a.prof_batch_bytes);
+  const int ncols = min(TW, a.ncol - c0);
+
   for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
+  for (int e = tid; e < a.lin * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c < ncols) {
+      C v = in[p * a.in_ls + c];
+      if (a.flags & PRO_CONJ) v = conjg(v);
+      if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      tile[p * LD + c] = v;
+    }
+  }
+  __syncthreads();
 
-  // persistent: tiles (column tile, other index, batch) strided over the grid
-  const int ntile_c = (a.ncol + TW - 1) / TW;
-  const long long ntiles = (long long)ntile_c * a.nother * a.nbatch;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int ct = (int)(t % ntile_c);
-    const int o = (int)((t / ntile_c) % a.nother);
-    const int bb = (int)(t / ((long long)ntile_c * a.nother));
-    if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) continue;   // block-uniform
-    const int c0 = ct * TW;
-    if (a.prof != nullptr && ct == 0 && o == 0 && tid == 0) atomicAdd(a.prof, a.prof_batch_bytes);
-    const int ncols = min(TW, a.ncol - c0);
-    __syncthreads();                           // previous tile's stores are done with `tile`
-    const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
-    for (int e = tid; e < a.lin * TW; e += nth) {
-      const int c = e % TW, p = e / TW;
-      if (c < ncols) {
-        C v = in[p * a.in_ls + c];
-        if (a.flags & PRO_CONJ) v = conjg(v);
-        if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-        tile[p * LD + c] = v;
+  const int br = brev5(lane);
+  for (int c = warp; c < ncols; c += nwarp) {
+    C v[R];
+    if (!a.inverse) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        v[j] = p < a.lin ? tile[p * LD + c] : make_float2(0.f, 0.f);
+      }
+      warp_fft_fwd<C, float, R>(v, lane, roots, N);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const int p = k1 + R * br;
+        if (p < a.lout) tile[p * LD + c] = v[k1];
+      }
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[(k1 + R * br) * LD + c];
+      warp_fft_inv<C, float, R>(v, lane, roots, N);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        if (p < a.lout) tile[p * LD + c] = v[j];
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
 
-    for (int c = warp; c < ncols; c += nwarp) {
-      C v[R];
-      if (!a.inverse) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int p = lane + 32 * j;
-          v[j] = p < a.lin ? tile[p * LD + c] : make_float2(0.f, 0.f);
-        }
-        warp_fft_fwd<C, float, R>(v, lane, roots, N);
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) {
-          const int p = k1 + R * br;
-          if (p < a.lout) tile[p * LD + c] = v[k1];
-        }
-      } else {
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[(k1 + R * br) * LD + c];
-        warp_fft_inv<C, float, R>(v, lane, roots, N);
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int p = lane + 32 * j;
-          if (p < a.lout) tile[p * LD + c] = v[j];
-        }
-      }
+  const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0;
+  C* out = a.out + obase;
+  for (int e = tid; e < a.lout * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c >= ncols) continue;
+    C v = a.scale * tile[p * LD + c];
+    if (a.flags & EPI_CONJ) v = conjg(v);
+    const long long oi = p * a.out_ls + c;
+    if (a.flags & (EPI_SUB | EPI_ADD)) {
+      if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      const C w = a.addend[obase + oi];
+      v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
     }
-    __syncthreads();
-
-    const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0;
-    C* out = a.out + obase;
-    for (int e = tid; e < a.lout * TW; e += nth) {
-      const int c = e % TW, p = e / TW;
-      if (c >= ncols) continue;
-      C v = a.scale * tile[p * LD + c];
-      if (a.flags & EPI_CONJ) v = conjg(v);
-      const long long oi = p * a.out_ls + c;
-      if (a.flags & (EPI_SUB | EPI_ADD)) {
-        if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-        const C w = a.addend[obase + oi];
-        v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
-      }
-      out[oi] = v;
-    }
+    out[oi] = v;
   }
 }
 
@@ -161,8 +156,7 @@ template <int R>
 static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
   constexpr int TW = 16;
   const size_t smem = (size_t)(32 * R * (TW + 1) + 32 * R) * sizeof(float2);
-  const long long tiles = (long long)((a.ncol + TW - 1) / TW) * a.nother * a.nbatch;
-  const int grid = persistent_grid((const void*)line_warp_kernel<R, TW>, 256, smem, tiles);
+  dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
   line_warp_kernel<R, TW><<<grid, 256, smem, s>>>(a);

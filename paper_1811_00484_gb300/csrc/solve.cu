@@ -53,12 +53,10 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict
                                                         long long N, int nchunk, double2* partial,
                                                         const int* active, unsigned long long* prof,
                                                         unsigned long long prof_bytes) {
-  __shared__ double2 red[kThreads / 32][129];
-  for (long long item = blockIdx.x; item < (long long)nchunk * B; item += gridDim.x) {
-  const int b = (int)(item / nchunk), chunk = (int)(item % nchunk);
-  if (!active[b]) continue;
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (!active[b]) return;
   if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
-  __syncthreads();                             // the previous item has finished with `red`
+  __shared__ double2 red[kThreads / 32][129];
   const long long base = (long long)chunk * kChunk;
   float2 wv[kPer];
   long long idxs[kPer];
@@ -97,7 +95,6 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict
     for (int q = 0; q < kThreads / 32; ++q) s = s + red[q][i];
     partial[((long long)b * 129 + i) * nchunk + chunk] = s;
   }
-  }
 }
 
 // w[b] -= sum_i coef[b][i] V_i[b]; optionally partial norms of the result
@@ -106,20 +103,14 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restri
                                                           long long N, int nchunk, double* nrm_partial,
                                                           const int* active, unsigned long long* prof,
                                                           unsigned long long prof_bytes) {
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  if (!active[b]) return;
+  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   __shared__ float2 c[129];
   __shared__ double red[kThreads / 32];
-  int cur_b = -1;
-  for (long long item = blockIdx.x; item < (long long)nchunk * B; item += gridDim.x) {
-  const int b = (int)(item / nchunk), chunk = (int)(item % nchunk);
-  if (!active[b]) continue;
-  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
-  if (b != cur_b) {                            // block-uniform
-    __syncthreads();
-    for (int i = threadIdx.x; i <= k; i += kThreads) {
-      const double2 v = coef[(long long)b * 129 + i];
-      c[i] = make_float2((float)v.x, (float)v.y);
-    }
-    cur_b = b;
+  for (int i = threadIdx.x; i <= k; i += kThreads) {
+    const double2 v = coef[(long long)b * 129 + i];
+    c[i] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
   const long long base = (long long)chunk * kChunk;
@@ -148,7 +139,6 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restri
       for (int q = 0; q < kThreads / 32; ++q) s += red[q];
       nrm_partial[(long long)b * nchunk + chunk] = s;
     }
-  }
   }
 }
 
@@ -677,20 +667,13 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   dim3 grid(nc, B);
   const int rblocks = (k + 1 + 7) / 8;
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
-  static int g_dots = 0, g_update = 0;
-  if (!g_dots) {
-    g_dots = persistent_grid((const void*)dots_kernel, kThreads, 0, 1LL << 40);
-    g_update = persistent_grid((const void*)update_kernel, kThreads, 0, 1LL << 40);
-  }
-  const int gd = (int)std::min<long long>(g_dots, (long long)nc * B);
-  const int gu = (int)std::min<long long>(g_update, (long long)nc * B);
   // classical Gram-Schmidt; a second pass only where the DGKS test asks for it
   for (int pass = 0; pass < passes; ++pass) {
     const int* mask = pass == 0 ? st->active : st->again;
     {
       ProfScope ps(PF_DOTS, s);
-      dots_kernel<<<gd, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, mask,
-                                          prof_bytes(PF_DOTS), (k + 2) * vec);
+      dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, mask,
+                                            prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
@@ -699,8 +682,8 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
     }
     {
       ProfScope ps(PF_UPDATE, s);
-      update_kernel<<<gu, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc, st->nrm_partial, mask,
-                                            prof_bytes(PF_UPDATE), (k + 3) * vec);
+      update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc, st->nrm_partial, mask,
+                                              prof_bytes(PF_UPDATE), (k + 3) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
