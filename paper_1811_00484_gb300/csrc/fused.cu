@@ -240,6 +240,8 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
   const int ix = warp / ny, iy = warp % ny;
   const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
   const int br = brev5(lane);
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, roots, P3);
   const long long line_off = ((long long)kx * a.P2 + ky) * n3;
   for (int b = 0; b < a.B; ++b) {
     if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
@@ -248,11 +250,11 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
     for (int comp = 0; comp < 3; ++comp) {
       const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < (R + 1) / 2; ++j) {
         const int p = lane + 32 * j;
         v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
       }
-      warp_fft_fwd<C, float, R>(v[comp], lane, roots, P3);
+      warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -282,10 +284,10 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
     }
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
-      warp_fft_inv<C, float, R>(v[comp], lane, roots, P3);
+      warp_fft_inv<C, float, R, true>(v[comp], lane, lc, roots, P3);
       C* dst = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < (R + 1) / 2; ++j) {
         const int p = lane + 32 * j;
         if (p < n3) dst[p] = v[comp][j];
       }

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
 // Forward transforms read the tile in natural order and write the
 // bit-reversed lane layout to its natural rows; inverse transforms read the
 // bit-reversed layout from the natural rows.
-template <int R, int TW>
+template <int R, int TW, bool HALF>
 __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a) {
   using C = float2;
   constexpr int N = 32 * R;
@@ -108,15 +108,17 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
   __syncthreads();
 
   const int br = brev5(lane);
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, roots, N);
   for (int c = warp; c < ncols; c += nwarp) {
     C v[R];
     if (!a.inverse) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
         const int p = lane + 32 * j;
         v[j] = p < a.lin ? tile[p * LD + c] : make_float2(0.f, 0.f);
       }
-      warp_fft_fwd<C, float, R>(v, lane, roots, N);
+      warp_fft_fwd<C, float, R, HALF>(v, lc, roots, N);
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) {
         const int p = k1 + R * br;
@@ -125,9 +127,9 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
     } else {
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[(k1 + R * br) * LD + c];
-      warp_fft_inv<C, float, R>(v, lane, roots, N);
+      warp_fft_inv<C, float, R, HALF>(v, lane, lc, roots, N);
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
         const int p = lane + 32 * j;
         if (p < a.lout) tile[p * LD + c] = v[j];
       }
@@ -159,7 +161,10 @@ static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
   dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
-  line_warp_kernel<R, TW><<<grid, 256, smem, s>>>(a);
+  // half-length lines: forward from n = N/2 points, or inverse cropped to N/2
+  const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
+  if (half) line_warp_kernel<R, TW, true><<<grid, 256, smem, s>>>(a);
+  else line_warp_kernel<R, TW, false><<<grid, 256, smem, s>>>(a);
 }
 
 static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
@@ -228,10 +233,14 @@ int line_fft_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "line kernel attributes");
 }
 

@@ -88,42 +88,104 @@ template <typename C, typename T> struct RegDft<C, T, 10> : RegDftSplit<C, T, 2,
 template <typename C, typename T> struct RegDft<C, T, 12> : RegDftSplit<C, T, 4, 3> {};
 template <typename C, typename T> struct RegDft<C, T, 16> : RegDftSplit<C, T, 4, 4> {};
 
-// forward: v[j] = x[lane + 32 j]  ->  v[k1] = X[k1 + R brev5(lane)]
-template <typename C, typename T, int R>
-__device__ __forceinline__ void warp_fft_fwd(C* v, int lane, const C* roots, int N) {
+// Per-lane constants of the lane transforms, computed once per kernel:
+//   tw[k1]  = w_N^{lane k1}                       (twiddle between the stages)
+//   fw[s]   = upper ? w_{2h}^i : 1, fs[s] = upper ? -1 : 1   (DIF stage s, h = 16 >> s)
+//   iw[s]   = (upper ? -1 : 1) conj(w_{2h}^i)                (DIT stage s, h = 1 << s)
+// with i = lane mod h and `upper` = bit h of the lane.
+template <typename C, typename T, int R> struct LaneConsts {
+  C tw[R > 1 ? R : 1];
+  C fw[5];
+  T fs[5];
+  C iw[5];
+  __device__ __forceinline__ void init(int lane, const C* roots, int N) {
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) tw[k1] = roots[lane * k1];
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int h = 16 >> st;
+      const bool up = (lane & h) != 0;
+      const C w = roots[(lane & (h - 1)) * (N / (2 * h))];
+      fw[st] = up ? w : mk((T)1, (T)0);
+      fs[st] = up ? (T)-1 : (T)1;
+    }
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int h = 1 << st;
+      const bool up = (lane & h) != 0;
+      const C w = conjg(roots[(lane & (h - 1)) * (N / (2 * h))]);
+      iw[st] = up ? mk(-w.x, -w.y) : w;
+    }
+  }
+};
+
+// forward: v[j] = x[lane + 32 j]  ->  v[k1] = X[k1 + R brev5(lane)].
+// HALF: only x[0 .. N/2) can be nonzero (zero-padded input): v[j] for
+// j >= (R+1)/2 (points lane + 32 j >= N/2 + 16) is set to zero here, so the
+// caller only loads j < (R+1)/2.
+template <typename C, typename T, int R, bool HALF = false>
+__device__ __forceinline__ void warp_fft_fwd(C* v, const LaneConsts<C, T, R>& lc, const C* roots,
+                                             int N) {
+  if (HALF) {
+#pragma unroll
+    for (int j = (R + 1) / 2; j < R; ++j) v[j] = mk((T)0, (T)0);
+  }
   reg_dft<C, T, R>(v, roots, N, false);
 #pragma unroll
-  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * roots[lane * k1];
+  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * lc.tw[k1];
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const int i = lane & (h - 1);
-    const bool upper = (lane & h) != 0;
-    const C w = roots[i * (N / (2 * h))];
+  for (int st = 0; st < 5; ++st) {
+    const int h = 16 >> st;
+    const T sg = lc.fs[st];
+    const C w = lc.fw[st];
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) {
       const C p = shfl_xor(v[k1], h);
-      v[k1] = upper ? (p - v[k1]) * w : v[k1] + p;
+      // lower lane: v + p; upper lane: (p - v) w
+      const C t = mk(fma(sg, v[k1].x, p.x), fma(sg, v[k1].y, p.y));
+      v[k1] = t * w;
     }
   }
 }
 
-// inverse (unscaled): v[k1] = X[k1 + R brev5(lane)]  ->  v[j] = N x[lane + 32 j]
-template <typename C, typename T, int R>
-__device__ __forceinline__ void warp_fft_inv(C* v, int lane, const C* roots, int N) {
+// inverse (unscaled): v[k1] = X[k1 + R brev5(lane)]  ->  v[j] = N x[lane + 32 j].
+// HALF: only x[0 .. N/2) is wanted (cropped output): the caller stores only
+// j < (R+1)/2.
+template <typename C, typename T, int R, bool HALF = false>
+__device__ __forceinline__ void warp_fft_inv(C* v, int lane, const LaneConsts<C, T, R>& lc,
+                                             const C* roots, int N) {
 #pragma unroll
-  for (int h = 1; h <= 16; h <<= 1) {
-    const int i = lane & (h - 1);
+  for (int st = 0; st < 5; ++st) {
+    const int h = 1 << st;
     const bool upper = (lane & h) != 0;
-    const C w = conjg(roots[i * (N / (2 * h))]);
+    const C w = lc.iw[st];
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) {
       const C p = shfl_xor(v[k1], h);
-      v[k1] = upper ? (p - w * v[k1]) : (v[k1] + w * p);
+      // lower lane: v + w p; upper lane: p - w v  (w carries the sign)
+      const C a = upper ? p : v[k1];
+      const C b = upper ? v[k1] : p;
+      v[k1] = cmadd(w, b, a);
     }
   }
 #pragma unroll
-  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * conjg(roots[lane * k1]);
+  for (int k1 = 1; k1 < R; ++k1) v[k1] = v[k1] * conjg(lc.tw[k1]);
   reg_dft<C, T, R>(v, roots, N, true);
+  (void)HALF;
+}
+
+// the original forms (per-call constants), kept for the FP64 and non-template users
+template <typename C, typename T, int R>
+__device__ __forceinline__ void warp_fft_fwd(C* v, int lane, const C* roots, int N) {
+  LaneConsts<C, T, R> lc;
+  lc.init(lane, roots, N);
+  warp_fft_fwd<C, T, R, false>(v, lc, roots, N);
+}
+template <typename C, typename T, int R>
+__device__ __forceinline__ void warp_fft_inv(C* v, int lane, const C* roots, int N) {
+  LaneConsts<C, T, R> lc;
+  lc.init(lane, roots, N);
+  warp_fft_inv<C, T, R, false>(v, lane, lc, roots, N);
 }
 
 // radices handled by the register path (N = 32 R <= 512)

@@ -32,6 +32,10 @@ HVOX = 5e-3
 K0 = K.wavenumber(F)
 
 GRIDS = [(3, 4, 5), (8, 8, 8), (6, 10, 20), (7, 5, 12), (16, 16, 16), (20, 9, 35)]
+# thin grids whose padded edges are 32 R for R = 2, 3, 5, 6, 8, 16: every radix of
+# the register-resident line and z-line FFTs, in both the x/y stages and z
+RADIX_GRIDS = [(48, 6, 32), (4, 80, 48), (6, 4, 80), (5, 6, 96), (4, 3, 128), (3, 4, 256),
+               (32, 3, 4)]
 
 
 def dev(a, dtype=torch.complex64):
@@ -118,6 +122,17 @@ def test_matvec_fp32_and_fp64_tucker(n):
     assert rel(y64, ref) <= 1e-11
     exact = M.matvec_fft(Ghat, J)
     assert rel(y64, exact) <= 1e-8 * 4          # HOSVD truncation at 1e-8
+
+
+@pytest.mark.parametrize("n", RADIX_GRIDS)
+def test_matvec_register_fft_radices(n):
+    T, Ghat, comp, rebuilt, op = setup_case(n, 1e-6)
+    J = rand_field(n, B=2, seed=11)
+    ref = M.matvec_fft(rebuilt, J)
+    assert rel(host(op.matvec(dev(J))), ref) <= 1e-5
+    assert rel(host(op.matvec(dev(J), path="uncompressed")), M.matvec_fft(Ghat, J)) <= 1e-5
+    y = rand_field(n, B=1, seed=12)
+    assert rel(host(op.matvec_adjoint(dev(y))), AD.adjoint_matvec(rebuilt, y)) <= 1e-5
 
 
 @pytest.mark.parametrize("n", [(3, 4, 5), (6, 10, 20), (16, 16, 16)])
