@@ -188,6 +188,11 @@ __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
 // right-hand side in registers.  Forward lane FFT, voxel-wise product in the
 // bit-reversed lane layout, inverse lane FFT: no shared-memory round trips
 // and no block barriers after the rebuild.
+// Slot of z-frequency k in a row of the rebuilt half fibre: one padding slot
+// every 8 entries, so the lanes' folded, bit-reversed frequencies (stride R)
+// fall in different banks (at most 2-way for the radices used, 4-way at R=10).
+__device__ __forceinline__ int ghalf_slot(int k) { return k + (k >> 3); }
+
 template <int R, bool STORED>
 __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> a) {
   using C = float2;
@@ -207,9 +212,10 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
     atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
   }
 
+  const int GS = ghalf_slot(H3 - 1) + 1;   // padded row length of the half fibre
   C* roots = reinterpret_cast<C*>(smem_raw);
-  C* ghalf = roots + P3;               // [6][H3]
-  C* wv = ghalf + 6 * H3;              // [6][r3max]
+  C* ghalf = roots + P3;               // [6][GS]
+  C* wv = ghalf + 6 * GS;              // [6][r3max]
   for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
   if (!STORED) {
     for (int it = tid; it < 6 * a.r3max; it += nth) {
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
       const C* w = wv + c * a.r3max;
       C acc = make_float2(0.f, 0.f);
       for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
-      ghalf[it] = acc;
+      ghalf[c * GS + ghalf_slot(kk)] = acc;
     }
   }
   __syncthreads();
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
           if (ix) s *= kParity[c][0];
           if (iy) s *= kParity[c][1];
           if (zm) s *= kParity[c][2];
-          const C gv = ghalf[c * H3 + fold];
+          const C gv = ghalf[c * GS + ghalf_slot(fold)];
           gc[c] = (s > 0) ? gv : make_float2(-gv.x, -gv.y);
         }
       }
@@ -297,7 +303,8 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
 
 template <int R, bool STORED>
 static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
-  const size_t smem = (size_t)(32 * R + 6 * a.H3 + 6 * a.r3max) * sizeof(float2);
+  const int GS = (a.H3 - 1) + ((a.H3 - 1) >> 3) + 1;
+  const size_t smem = (size_t)(32 * R + 6 * GS + 6 * a.r3max) * sizeof(float2);
   const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
   a.prof = prof_bytes(fam);
   a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);

@@ -75,14 +75,23 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
 // Forward transforms read the tile in natural order and write the
 // bit-reversed lane layout to its natural rows; inverse transforms read the
 // bit-reversed layout from the natural rows.
+// Tile slot of element (row p, column c): rows of TW = 16 columns with the
+// column index XOR-swizzled by (p ^ p>>4 ^ p>>6) mod 16.  Row-wise loads and
+// stores stay conflict-free (a permutation within the row), and so do the
+// warps' column accesses at natural rows lane + 32 j and at bit-reversed rows
+// k1 + R brev5(lane) for every power-of-two R (at most 3-way otherwise).
+__device__ __forceinline__ int tile_slot(int p, int c) {
+  return p * 16 + (c ^ ((p ^ (p >> 4) ^ (p >> 6)) & 15));
+}
+
 template <int R, int TW, bool HALF>
 __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a) {
+  static_assert(TW == 16, "the tile swizzle assumes 16 columns");
   using C = float2;
   constexpr int N = 32 * R;
-  constexpr int LD = TW + 1;                 // odd stride: column reads are conflict-free
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = reinterpret_cast<C*>(smem_raw);  // element (row p, column c) at p * LD + c
-  C* roots = tile + N * LD;
+  C* tile = reinterpret_cast<C*>(smem_raw);  // element (row p, column c) at tile_slot(p, c)
+  C* roots = tile + N * TW;
 
   const int c0 = blockIdx.x * TW;
   const int o = blockIdx.y;
@@ -102,7 +111,7 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
       C v = in[p * a.in_ls + c];
       if (a.flags & PRO_CONJ) v = conjg(v);
       if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-      tile[p * LD + c] = v;
+      tile[tile_slot(p, c)] = v;
     }
   }
   __syncthreads();
@@ -116,22 +125,22 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
 #pragma unroll
       for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
         const int p = lane + 32 * j;
-        v[j] = p < a.lin ? tile[p * LD + c] : make_float2(0.f, 0.f);
+        v[j] = p < a.lin ? tile[tile_slot(p, c)] : make_float2(0.f, 0.f);
       }
       warp_fft_fwd<C, float, R, HALF>(v, lc, roots, N);
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) {
         const int p = k1 + R * br;
-        if (p < a.lout) tile[p * LD + c] = v[k1];
+        if (p < a.lout) tile[tile_slot(p, c)] = v[k1];
       }
     } else {
 #pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[(k1 + R * br) * LD + c];
+      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[tile_slot(k1 + R * br, c)];
       warp_fft_inv<C, float, R, HALF>(v, lane, lc, roots, N);
 #pragma unroll
       for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
         const int p = lane + 32 * j;
-        if (p < a.lout) tile[p * LD + c] = v[j];
+        if (p < a.lout) tile[tile_slot(p, c)] = v[j];
       }
     }
   }
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
   for (int e = tid; e < a.lout * TW; e += nth) {
     const int c = e % TW, p = e / TW;
     if (c >= ncols) continue;
-    C v = a.scale * tile[p * LD + c];
+    C v = a.scale * tile[tile_slot(p, c)];
     if (a.flags & EPI_CONJ) v = conjg(v);
     const long long oi = p * a.out_ls + c;
     if (a.flags & (EPI_SUB | EPI_ADD)) {
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a)
 template <int R>
 static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
   constexpr int TW = 16;
-  const size_t smem = (size_t)(32 * R * (TW + 1) + 32 * R) * sizeof(float2);
+  const size_t smem = (size_t)(32 * R * TW + 32 * R) * sizeof(float2);
   dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
