@@ -1,0 +1,167 @@
+"""Parity at the workloads' full sizes, in the launch shapes the benchmark uses.
+
+The oracle cannot run whole operators at these sizes, so it computes sampled
+outputs one by one: the BTTB sum at a sampled voxel m is
+  (G J)_a[m] = sum_b sum_{m'} T_ab(m - m') J_b[m'],
+with T from oracle.kernel (dyadic kernel times h^3, self term at m' = m).
+Properties that hold at any size cover the rest (residuals of the GPU's own
+FP64 operator, finite differences of the loss).
+Tolerances: sampled FP32 matvec outputs are compared relative to the RMS of
+the whole output (1e-5 plus the HOSVD truncation tolerance); FP64 ones to 1e-9.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import adjoint as AD
+from oracle import embed as E
+from oracle import kernel as K
+from oracle import matvec as M
+
+vie = pytest.importorskip("paper_1811_00484_gb300")
+pytestmark = pytest.mark.gpu
+C128 = torch.complex128
+
+
+def dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def sampled_product(n, h, k0, J, voxels):
+    """Oracle BTTB product at the listed voxels, for every right-hand side of J."""
+    n1, n2, n3 = n
+    I, Jg, Kg = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    out = []
+    for m in voxels:
+        R = np.stack([(m[0] - I) * h, (m[1] - Jg) * h, (m[2] - Kg) * h], axis=-1)
+        R[m] = (1.0, 0.0, 0.0)                       # placeholder for the zero offset
+        T = K.dyadic(R, k0) * h ** 3
+        s = K.self_term(h, k0)
+        for c, (a, b) in enumerate(K.COMPONENTS):
+            T[(c,) + tuple(m)] = s if a == b else 0.0
+        y = np.zeros((J.shape[0], 3), dtype=np.complex128)
+        for a in range(3):
+            for b in range(3):
+                y[:, a] += np.einsum("xyz,Bxyz->B", T[K.component_index(a, b)], J[:, b])
+        out.append(y)
+    return np.stack(out, axis=1)                     # [B, nsample, 3]
+
+
+def pick_voxels(n, count, seed):
+    rng = np.random.default_rng(seed)
+    vox = [tuple(int(rng.integers(0, v)) for v in n) for _ in range(count - 2)]
+    return vox + [(0, 0, 0), tuple(v - 1 for v in n)]
+
+
+def test_ring_dipoles_n96_batch16():
+    wl = workloads.dipoles_n96()
+    n, h = wl.n, wl.h
+    k0 = K.wavenumber(wl.freq_hz)
+    op = vie.Operator(n, h, wl.freq_hz, wl.tol_svd)
+    B = wl.dipoles.shape[0]
+    assert B == 16
+    # incident fields at sampled voxels
+    einc = op.incident_dipole(wl.dipoles, dtype=C128)
+    vox = pick_voxels(n, 6, 1)
+    x = (np.arange(n[0]) + 0.5 - 0.5 * n[0]) * h
+    pts = np.array([[x[i], x[j], x[k]] for i, j, k in vox])
+    e_h = host(einc)
+    for b in range(B):
+        ref = K.dipole_field(pts, wl.dipoles[b], k0)            # [3, nsample]
+        got = np.stack([e_h[b, :, i, j, k] for i, j, k in vox], axis=1)
+        assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    # batched FP32 matvec (the bench's launch shape for batched RHS) at sampled voxels
+    J = wl.J[:1].repeat(B, axis=0) * np.arange(1, B + 1)[:, None, None, None, None]
+    Y = host(op.matvec(dev(J)))
+    ref = sampled_product(n, h, k0, J, vox)
+    got = np.stack([Y[:, :, i, j, k] for i, j, k in vox], axis=1)
+    scale = np.sqrt(np.mean(np.abs(Y) ** 2, axis=(1, 2, 3, 4)))[:, None, None]
+    assert np.max(np.abs(got - ref) / scale) <= 1e-5 + 4 * wl.tol_svd
+    # one batched solve of the 16 dipole fields to 1e-6 (FP64 refinement)
+    chi = dev(wl.chi, C128)
+    w, info = op.solve(chi, einc, tol=1e-6)
+    assert info["converged"], info
+    b = chi[None, None] * einc
+    r = b - op.apply_system(chi, w)
+    rel = torch.linalg.vector_norm(r.reshape(B, -1), dim=1) / torch.linalg.vector_norm(b.reshape(B, -1), dim=1)
+    assert float(rel.max()) <= 1e-6
+    # the FP64 operator that certified the residual, against the oracle at sampled voxels
+    Gw = host(op.matvec(w))
+    refw = sampled_product(n, h, k0, host(w)[:2], vox[:3])
+    gotw = np.stack([Gw[:2, :, i, j, k] for i, j, k in vox[:3]], axis=1)
+    scale = np.sqrt(np.mean(np.abs(Gw[:2]) ** 2, axis=(1, 2, 3, 4)))[:, None, None]
+    assert np.max(np.abs(gotw - refw) / scale) <= 4 * wl.tol_svd
+    op.close()
+
+
+def test_memory_headline_n256():
+    wl = workloads.memory_n256()
+    n, h = wl.n, wl.h
+    k0 = K.wavenumber(wl.freq_hz)
+    op = vie.Operator(n, h, wl.freq_hz, wl.tol_svd)
+    info = op.info()
+    assert info["uncompressed_bytes"] == 6 * 512 ** 3 * 8
+    assert info["tucker_bytes"] * 1000 < info["uncompressed_bytes"]
+    J = wl.J[:1]
+    Y = host(op.matvec(dev(J)))
+    vox = pick_voxels(n, 2, 3)
+    ref = sampled_product(n, h, k0, J, vox)
+    got = np.stack([Y[:, :, i, j, k] for i, j, k in vox], axis=1)
+    scale = np.sqrt(np.mean(np.abs(Y) ** 2))
+    assert np.max(np.abs(got - ref)) / scale <= 1e-5 + 4 * wl.tol_svd
+    op.close()
+
+
+def test_gradient_n64_against_finite_differences():
+    """Adjoint gradient through the solve vs FP64 central differences (step 1e-4)."""
+    wl = workloads.gradient_n64()
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd)
+    opts = dict(tol=1e-12, max_refine=40)
+    einc = dev(wl.einc, C128)
+    with torch.no_grad():
+        E_t = vie.solve_fields(op, dev(wl.extras["chi_target"], C128), einc, **opts)
+    chi = dev(wl.chi, C128).requires_grad_(True)
+    loss = torch.sum(torch.abs(vie.solve_fields(op, chi, einc, **opts) - E_t) ** 2)
+    loss.backward()
+    g = chi.grad.detach().cpu().numpy()
+    step = 1e-4
+    an, fd = [], []
+    for v in wl.extras["probe_voxels"]:
+        idx = np.unravel_index(int(v), wl.chi.shape)
+        for unit in (1.0, 1j):
+            vals = []
+            for sgn in (1, -1):
+                c = wl.chi.copy()
+                c[idx] += sgn * unit * step
+                with torch.no_grad():
+                    Ee = vie.solve_fields(op, dev(c, C128), einc, **opts)
+                    vals.append(torch.sum(torch.abs(Ee - E_t) ** 2).item())
+            fd.append((vals[0] - vals[1]) / (2 * step))
+            an.append(g[idx].real if unit == 1.0 else g[idx].imag)
+    an, fd = np.array(an), np.array(fd)
+    assert np.linalg.norm(an - fd) <= 1e-4 * np.linalg.norm(fd)
+    assert np.all(np.abs(an - fd) <= 1e-3 * np.abs(fd) + 1e-4 * np.linalg.norm(fd) / np.sqrt(fd.size))
+    op.close()
+
+
+def test_gradient_n16_against_oracle_adjoint_gradient():
+    """The gradient workload's recipe at 16^3: GPU adjoint gradient vs the oracle's."""
+    wl = workloads.gradient_n64(n=16)
+    k0 = K.wavenumber(wl.freq_hz)
+    Ghat = E.green_spectra(K.toeplitz_tensor(*wl.n, wl.h, k0), *wl.n)
+    _, E_t, _ = AD.forward(Ghat, wl.extras["chi_target"], wl.einc, tol=1e-12)
+    L_o, g_o, _, _ = AD.gradient(Ghat, wl.chi, wl.einc, E_t)
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, 1e-10)
+    chi = dev(wl.chi, C128).requires_grad_(True)
+    Ef = vie.solve_fields(op, chi, dev(wl.einc, C128), tol=1e-12, max_refine=40)
+    loss = torch.sum(torch.abs(Ef - dev(E_t, C128)) ** 2)
+    loss.backward()
+    g = chi.grad.detach().cpu().numpy()
+    assert abs(loss.item() - L_o) <= 1e-6 * L_o
+    assert np.linalg.norm(g - g_o) <= 1e-5 * np.linalg.norm(g_o)
+    op.close()
