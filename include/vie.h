@@ -107,6 +107,9 @@ typedef struct vie_op_info_t {
     size_t workspace_bytes;      /* scratch currently held                      */
     int has_uncompressed;        /* VIE_STORE_UNCOMPRESSED was given            */
     int max_batch;               /* batch size the scratch is sized for         */
+    int line_threads[4];         /* CTA size of the x, y, inverse y, inverse x
+                                    FFT stages (vie_autotune's choice)          */
+    int tuned_batch;             /* batch vie_autotune timed at (0 = defaults)  */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */
@@ -205,6 +208,29 @@ int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
  */
 int vie_matvec_noalloc(const vie_op* op, const void* J, void* Y, int B,
                        void* stream);
+
+/*
+ * Y_p = G_p J_p for `count` operators at once, c64, Tucker path: the batched
+ * and mixed-size counterpart of vie_matvec (Section V.B for each operator).
+ * Grids of different sizes, each with its own batch B[p], go through one
+ * launch per stage (slab cores, x, y, fused z/rebuild/product, inverse y,
+ * inverse x) when every padded edge 2 n_q is 32 R with R in {1..6, 8};
+ * otherwise (or for count > 8, in groups of 8) through the per-operator path.
+ * ops, J, Y, B: host arrays of `count` entries; J[p], Y[p]: device
+ * [B[p]][3][n1][n2][n3] of operator p.  Operators must be distinct (each
+ * uses its own scratch).
+ */
+int vie_matvec_multi(const vie_op* const* ops, const void* const* J,
+                     void* const* Y, const int* B, int count, void* stream);
+
+/*
+ * Pick the CTA size (64, 128 or 256 threads) of each register-path FFT
+ * stage of `op` by timing FP32 Tucker matvecs at batch B on `stream`, and
+ * keep the fastest (vie_op_info reports the choice).  Allocates two
+ * temporary batches; synchronises `stream`.  Results of later calls do not
+ * change, only their speed.
+ */
+int vie_autotune(vie_op* op, int B, void* stream);
 
 /* X = G^H Y = conj(G conj(Y)) (G is complex symmetric).  Layout as vie_matvec. */
 int vie_matvec_adjoint(const vie_op* op, const void* Y, void* X, int B,

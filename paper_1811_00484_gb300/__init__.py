@@ -36,7 +36,7 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_reserve", "vie_matvec", "vie_matvec_adjoint", "vie_apply_system",
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
-           "vie_profile_stop", "vie_matvec_noalloc")
+           "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune")
 
 
 class VieError(RuntimeError):
@@ -54,7 +54,8 @@ class OpInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("P", ctypes.c_int * 3), ("ranks", (ctypes.c_int * 3) * 6),
                 ("tucker_bytes", ctypes.c_size_t), ("tucker_bytes_full", ctypes.c_size_t),
                 ("uncompressed_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
-                ("has_uncompressed", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("has_uncompressed", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -90,6 +91,9 @@ def _load():
         "vie_matvec": [vp, vp, vp, ci, ci, ci, vp],
         "vie_matvec_adjoint": [vp, vp, vp, ci, ci, ci, vp],
         "vie_matvec_noalloc": [vp, vp, vp, ci, vp],
+        "vie_matvec_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                             ctypes.POINTER(ci), ci, vp],
+        "vie_autotune": [vp, ci, vp],
         "vie_apply_system": [vp, vp, vp, vp, ci, ci, ci, ci, vp],
         "vie_total_field": [vp, vp, vp, vp, ci, ci, ci, vp],
         "vie_solve": [vp, vp, vp, vp, ci, ci, ci, ctypes.POINTER(SolveOpts),
@@ -198,7 +202,8 @@ class Operator:
                 "tucker_bytes": inf.tucker_bytes, "tucker_bytes_full": inf.tucker_bytes_full,
                 "uncompressed_bytes": inf.uncompressed_bytes,
                 "workspace_bytes": inf.workspace_bytes,
-                "has_uncompressed": bool(inf.has_uncompressed), "max_batch": inf.max_batch}
+                "has_uncompressed": bool(inf.has_uncompressed), "max_batch": inf.max_batch,
+                "line_threads": tuple(inf.line_threads), "tuned_batch": inf.tuned_batch}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""
@@ -215,6 +220,11 @@ class Operator:
 
     def reserve(self, max_batch):
         _check(lib.vie_reserve(self._h, int(max_batch)), "vie_reserve")
+
+    def autotune(self, batch=1):
+        """Pick the FFT stages' CTA sizes by timing matvecs at `batch` (vie_autotune)."""
+        _check(lib.vie_autotune(self._h, int(batch), _stream()), "vie_autotune")
+        return self.info()["line_threads"]
 
     # -- operator applications ---------------------------------------------
     def _out(self, like, out):
@@ -307,6 +317,24 @@ class Operator:
 PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy", "line_ix",
                     "slab_cores", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
                     "setup")
+
+
+def matvec_multi(ops, Js, outs=None):
+    """Y_p = G_p J_p for several operators (grids may differ) in one launch per stage."""
+    torch = _torch()
+    count = len(ops)
+    if len(Js) != count:
+        raise ValueError("one current per operator")
+    outs = [torch.empty_like(J) for J in Js] if outs is None else outs
+    for J in Js:
+        if J.dtype != torch.complex64:
+            raise TypeError("vie_matvec_multi takes complex64")
+    hs = (ctypes.c_void_p * count)(*[op._h.value for op in ops])
+    jp = (ctypes.c_void_p * count)(*[_dev(J, "J", op.n).value for op, J in zip(ops, Js)])
+    yp = (ctypes.c_void_p * count)(*[_dev(Y, "out", op.n).value for op, Y in zip(ops, outs)])
+    bs = (ctypes.c_int * count)(*[_batch(J, op.n) for op, J in zip(ops, Js)])
+    _check(lib.vie_matvec_multi(hs, jp, yp, bs, count, _stream()), "vie_matvec_multi")
+    return outs
 
 
 def profile_start(families=None):

@@ -171,6 +171,8 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   r.workspace_bytes = op->ws.bytes + op->solve_ws.bytes;
   r.has_uncompressed = op->spec32 != nullptr;
   r.max_batch = op->ws_batch;
+  for (int i = 0; i < 4; ++i) r.line_threads[i] = op->tune.line_threads[i];
+  r.tuned_batch = op->tune.tuned_batch;
   *info = r;
   return VIE_OK;
 }

@@ -12,60 +12,16 @@
 // with signs, for the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2) of every
 // right-hand side.  The stored (uncompressed) variant reads the six spectra
 // from memory instead.
-#include "warpfft.cuh"
+#include "stages.cuh"
 
 namespace vie {
-
-// sign of component c (xx, xy, xz, yy, yz, zz) under k_q -> P_q - k_q
-__constant__ int kParity[6][3] = {
-    {1, 1, 1}, {-1, -1, 1}, {-1, 1, -1}, {1, 1, 1}, {1, -1, -1}, {1, 1, 1}};
-
-template <typename T> struct SlabArgs {
-  const cx<T>* core[6];
-  const cx<T>* U1[6];
-  int r1[6], r2[6], r3[6];
-  cx<T>* slab;
-  long long slab_stride;
-  int r2max, r3max;
-  unsigned long long* prof;
-  unsigned long long prof_launch_bytes;
-};
 
 template <typename T>
 __global__ void __launch_bounds__(256) slab_core_kernel(const SlabArgs<T> a) {
   if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(a.prof, a.prof_launch_bytes);
-  using C = cx<T>;
-  const int k1 = blockIdx.x, c = blockIdx.y;
-  const int r1 = a.r1[c], r2 = a.r2[c], r3 = a.r3[c];
-  const C* core = a.core[c];
-  const C* u1 = a.U1[c] + (long long)k1 * r1;
-  C* S = a.slab + c * a.slab_stride + (long long)k1 * a.r2max * a.r3max;
-  for (int it = threadIdx.x; it < r2 * r3; it += blockDim.x) {
-    const int b = it / r3, g = it % r3;
-    C acc = czero<C>();
-    for (int al = 0; al < r1; ++al) acc = cmadd(u1[al], core[(al * r2 + b) * r3 + g], acc);
-    S[b * a.r3max + g] = acc;
-  }
+  slab_core_block<T>(a, blockIdx.x, blockIdx.y);
 }
-
-template <typename T> struct FusedArgs {
-  cx<T>* data;                 // [B*3][P1][P2][n3], transformed in place
-  const cx<T>* roots;          // P3-th roots of unity
-  FftPlan plan;
-  int n3, P1, P2, P3, H1, H2, H3;
-  int B;
-  long long comp_stride;       // P1 * P2 * n3
-  const CompMeta<T>* meta;     // [6] (Tucker)
-  int r2max, r3max;
-  const cx<T>* spec;           // [6][P1][P2][P3] (stored)
-  long long spec_stride;       // P1 * P2 * P3
-  const int* active;           // per RHS, nullptr = all
-  int lines_per_round;         // z-lines (x3 components) held in shared memory at once
-  int ld;                      // shared-memory line stride
-  unsigned long long* prof;    // profiler byte counter (nullptr = off)
-  unsigned long long prof_rhs_bytes, prof_launch_bytes;
-};
 
 template <typename T, bool STORED>
 __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
@@ -156,9 +112,9 @@ __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             int s = 1;
-            if (ix) s *= kParity[c][0];
-            if (iy) s *= kParity[c][1];
-            if (zm) s *= kParity[c][2];
+            if (ix) s *= parity_sign(c, 0);
+            if (iy) s *= parity_sign(c, 1);
+            if (zm) s *= parity_sign(c, 2);
             const C v = ghalf[c * H3 + fold];
             gc[c] = (s > 0) ? v : mk(-v.x, -v.y);
           }
@@ -184,127 +140,16 @@ __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
 }
 
 // Register-resident variant for P3 = 32 R: one CTA of four warps per (k1, k2)
-// group, one warp per mirror z-line holding the three components of every
-// right-hand side in registers.  Forward lane FFT, voxel-wise product in the
-// bit-reversed lane layout, inverse lane FFT: no shared-memory round trips
-// and no block barriers after the rebuild.
-// Slot of z-frequency k in a row of the rebuilt half fibre: one padding slot
-// every 8 entries, so the lanes' folded, bit-reversed frequencies (stride R)
-// fall in different banks (at most 2-way for the radices used, 4-way at R=10).
-__device__ __forceinline__ int ghalf_slot(int k) { return k + (k >> 3); }
-
+// mirror group, see fused_warp_group.
 template <int R, bool STORED>
 __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> a) {
-  using C = float2;
-  constexpr int P3 = 32 * R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int n3 = a.n3, H3 = a.H3;
-  const int g = blockIdx.x;
-  const int k1 = g / a.H2, k2 = g % a.H2;
-  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
-  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
-  const int nl = nx * ny;
-  if (a.prof != nullptr && blockIdx.x == 0 && tid == 0) {
-    unsigned long long nb = 0;
-    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
-    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
-  }
-
-  const int GS = ghalf_slot(H3 - 1) + 1;   // padded row length of the half fibre
-  C* roots = reinterpret_cast<C*>(smem_raw);
-  C* ghalf = roots + P3;               // [6][GS]
-  C* wv = ghalf + 6 * GS;              // [6][r3max]
-  for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
-  if (!STORED) {
-    for (int it = tid; it < 6 * a.r3max; it += nth) {
-      const int c = it / a.r3max, gm = it % a.r3max;
-      const CompMeta<float> m = a.meta[c];
-      C acc = make_float2(0.f, 0.f);
-      if (gm < m.r3) {
-        const C* S = m.slab + (long long)k1 * a.r2max * a.r3max;
-        const C* u2 = m.U2 + (long long)k2 * m.r2;
-        for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max + gm], acc);
-      }
-      wv[it] = acc;
-    }
-    __syncthreads();
-    for (int it = tid; it < 6 * H3; it += nth) {
-      const int c = it / H3, kk = it % H3;
-      const CompMeta<float> m = a.meta[c];
-      const C* u3 = m.U3 + (long long)kk * m.r3;
-      const C* w = wv + c * a.r3max;
-      C acc = make_float2(0.f, 0.f);
-      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
-      ghalf[c * GS + ghalf_slot(kk)] = acc;
-    }
-  }
-  __syncthreads();
-  if (warp >= nl) return;                  // no block barrier follows
-
-  const int ix = warp / ny, iy = warp % ny;
-  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
-  const int br = brev5(lane);
-  LaneConsts<C, float, R> lc;
-  lc.init(lane, roots, P3);
-  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
-  for (int b = 0; b < a.B; ++b) {
-    if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
-    C v[3][R];
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-#pragma unroll
-      for (int j = 0; j < (R + 1) / 2; ++j) {
-        const int p = lane + 32 * j;
-        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
-      }
-      warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int kk = q + R * br;                       // z-frequency held in register q
-      C gc[6];
-      if (STORED) {
-        const long long off = ((long long)kx * a.P2 + ky) * P3 + kk;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) gc[c] = a.spec[c * a.spec_stride + off];
-      } else {
-        const bool zm = 2 * kk > P3;
-        const int fold = zm ? P3 - kk : kk;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          int s = 1;
-          if (ix) s *= kParity[c][0];
-          if (iy) s *= kParity[c][1];
-          if (zm) s *= kParity[c][2];
-          const C gv = ghalf[c * GS + ghalf_slot(fold)];
-          gc[c] = (s > 0) ? gv : make_float2(-gv.x, -gv.y);
-        }
-      }
-      const C jx = v[0][q], jy = v[1][q], jz = v[2][q];
-      v[0][q] = gc[0] * jx + gc[1] * jy + gc[2] * jz;
-      v[1][q] = gc[1] * jx + gc[3] * jy + gc[4] * jz;
-      v[2][q] = gc[2] * jx + gc[4] * jy + gc[5] * jz;
-    }
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      warp_fft_inv<C, float, R, true>(v[comp], lane, lc, roots, P3);
-      C* dst = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-#pragma unroll
-      for (int j = 0; j < (R + 1) / 2; ++j) {
-        const int p = lane + 32 * j;
-        if (p < n3) dst[p] = v[comp][j];
-      }
-    }
-  }
+  fused_warp_group<R, STORED>(a, blockIdx.x, reinterpret_cast<float2*>(smem_raw));
 }
 
 template <int R, bool STORED>
 static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
-  const int GS = (a.H3 - 1) + ((a.H3 - 1) >> 3) + 1;
-  const size_t smem = (size_t)(32 * R + 6 * GS + 6 * a.r3max) * sizeof(float2);
+  const size_t smem = fused_warp_smem(R, a.H3, a.r3max);
   const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
   a.prof = prof_bytes(fam);
   a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);
@@ -364,7 +209,7 @@ static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
 // host launchers used by matvec.cu
 // ---------------------------------------------------------------------------
 template <typename T>
-int launch_slab_cores(const vie_op* op, cudaStream_t s) {
+vie::SlabArgs<T> make_slab_args(const vie_op* op) {
   vie::SlabArgs<T> a;
   for (int c = 0; c < 6; ++c) {
     const TuckerComp& tc = op->comp[c];
@@ -385,6 +230,12 @@ int launch_slab_cores(const vie_op* op, cudaStream_t s) {
   a.r3max = op->rmax[2];
   a.prof = prof_bytes(PF_SLAB);
   a.prof_launch_bytes = 6ull * op->slab_stride * sizeof(cx<T>);
+  return a;
+}
+
+template <typename T>
+int launch_slab_cores(const vie_op* op, cudaStream_t s) {
+  vie::SlabArgs<T> a = make_slab_args<T>(op);
   dim3 grid(op->H[0], 6);
   ProfScope ps(PF_SLAB, s);
   vie::slab_core_kernel<T><<<grid, 256, 0, s>>>(a);
@@ -392,9 +243,9 @@ int launch_slab_cores(const vie_op* op, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
-                 cudaStream_t s) {
-  vie::FusedArgs<T> a;
+vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool stored,
+                                  const int* active) {
+  vie::FusedArgs<T> a = {};
   a.data = data;
   if constexpr (sizeof(T) == 4) {
     a.roots = op->roots32[2];
@@ -422,6 +273,18 @@ int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* a
   a.active = active;
   a.ld = op->P[2];
   a.lines_per_round = 4;
+  const int fam = stored ? PF_FUSED_STORED : PF_FUSED_TUCKER;
+  a.prof = prof_bytes(fam);
+  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(cx<T>);
+  a.prof_launch_bytes = stored ? 6ull * a.spec_stride * sizeof(cx<T>) : 0ull;
+  (void)stored;
+  return a;
+}
+
+template <typename T>
+int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
+                 cudaStream_t s) {
+  vie::FusedArgs<T> a = make_fused_args<T>(op, data, B, stored, active);
   if (stored) {
     if (a.spec == nullptr) {
       set_error("operator was built without VIE_STORE_UNCOMPRESSED");
@@ -442,6 +305,8 @@ int fused_init_attributes() {
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");
 }
 
+template vie::SlabArgs<float> make_slab_args<float>(const vie_op*);
+template vie::FusedArgs<float> make_fused_args<float>(const vie_op*, float2*, int, bool, const int*);
 template int launch_slab_cores<float>(const vie_op*, cudaStream_t);
 template int launch_slab_cores<double>(const vie_op*, cudaStream_t);
 template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t);

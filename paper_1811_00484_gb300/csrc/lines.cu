@@ -8,7 +8,7 @@
 // (points lin..N-1 read as zero), cropping (only points < lout stored),
 // conjugation, the contrast product and the final scale/subtract of the
 // system operator are fused into the load and store loops.
-#include "warpfft.cuh"
+#include "stages.cuh"
 
 namespace vie {
 
@@ -68,112 +68,26 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
   }
 }
 
-// Register-resident variant for N = 32 R (columns contiguous in memory): the
-// CTA stages a tile of TW columns in shared memory (coalesced rows), each
-// warp pulls whole columns into registers, transforms them with the lane FFT
-// and writes them back, so the tile is touched by two block barriers only.
-// Forward transforms read the tile in natural order and write the
-// bit-reversed lane layout to its natural rows; inverse transforms read the
-// bit-reversed layout from the natural rows.
-// Tile slot of element (row p, column c): rows of TW = 16 columns with the
-// column index XOR-swizzled by (p ^ p>>4 ^ p>>6) mod 16.  Row-wise loads and
-// stores stay conflict-free (a permutation within the row), and so do the
-// warps' column accesses at natural rows lane + 32 j and at bit-reversed rows
-// k1 + R brev5(lane) for every power-of-two R (at most 3-way otherwise).
-__device__ __forceinline__ int tile_slot(int p, int c) {
-  return p * 16 + (c ^ ((p ^ (p >> 4) ^ (p >> 6)) & 15));
-}
-
-template <int R, int TW, bool HALF>
+// Register-resident variant for N = 32 R (columns contiguous in memory): one
+// 16-column tile per CTA, see line_warp_tile.
+template <int R, bool HALF>
 __global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a) {
-  static_assert(TW == 16, "the tile swizzle assumes 16 columns");
-  using C = float2;
-  constexpr int N = 32 * R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = reinterpret_cast<C*>(smem_raw);  // element (row p, column c) at tile_slot(p, c)
-  C* roots = tile + N * TW;
-
-  const int c0 = blockIdx.x * TW;
-  const int o = blockIdx.y;
-  const int bb = blockIdx.z;
-  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  if (a.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0)
-    atomicAdd(a.prof, a.prof_batch_bytes);
-  const int ncols = min(TW, a.ncol - c0);
-
-  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
-  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
-  for (int e = tid; e < a.lin * TW; e += nth) {
-    const int c = e % TW, p = e / TW;
-    if (c < ncols) {
-      C v = in[p * a.in_ls + c];
-      if (a.flags & PRO_CONJ) v = conjg(v);
-      if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-      tile[tile_slot(p, c)] = v;
-    }
-  }
-  __syncthreads();
-
-  const int br = brev5(lane);
-  LaneConsts<C, float, R> lc;
-  lc.init(lane, roots, N);
-  for (int c = warp; c < ncols; c += nwarp) {
-    C v[R];
-    if (!a.inverse) {
-#pragma unroll
-      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
-        const int p = lane + 32 * j;
-        v[j] = p < a.lin ? tile[tile_slot(p, c)] : make_float2(0.f, 0.f);
-      }
-      warp_fft_fwd<C, float, R, HALF>(v, lc, roots, N);
-#pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) {
-        const int p = k1 + R * br;
-        if (p < a.lout) tile[tile_slot(p, c)] = v[k1];
-      }
-    } else {
-#pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[tile_slot(k1 + R * br, c)];
-      warp_fft_inv<C, float, R, HALF>(v, lane, lc, roots, N);
-#pragma unroll
-      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
-        const int p = lane + 32 * j;
-        if (p < a.lout) tile[tile_slot(p, c)] = v[j];
-      }
-    }
-  }
-  __syncthreads();
-
-  const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0;
-  C* out = a.out + obase;
-  for (int e = tid; e < a.lout * TW; e += nth) {
-    const int c = e % TW, p = e / TW;
-    if (c >= ncols) continue;
-    C v = a.scale * tile[tile_slot(p, c)];
-    if (a.flags & EPI_CONJ) v = conjg(v);
-    const long long oi = p * a.out_ls + c;
-    if (a.flags & (EPI_SUB | EPI_ADD)) {
-      if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-      const C w = a.addend[obase + oi];
-      v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
-    }
-    out[oi] = v;
-  }
+  line_warp_tile<R, HALF>(a, blockIdx.x * kLineTile, blockIdx.y, blockIdx.z,
+                          reinterpret_cast<float2*>(smem_raw));
 }
 
 template <int R>
 static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
-  constexpr int TW = 16;
-  const size_t smem = (size_t)(32 * R * TW + 32 * R) * sizeof(float2);
-  dim3 grid((a.ncol + TW - 1) / TW, a.nother, a.nbatch);
+  const size_t smem = line_warp_smem(R);
+  dim3 grid((a.ncol + kLineTile - 1) / kLineTile, a.nother, a.nbatch);
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
+  const int threads = a.threads > 0 ? a.threads : 256;
   // half-length lines: forward from n = N/2 points, or inverse cropped to N/2
   const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
-  if (half) line_warp_kernel<R, TW, true><<<grid, 256, smem, s>>>(a);
-  else line_warp_kernel<R, TW, false><<<grid, 256, smem, s>>>(a);
+  if (half) line_warp_kernel<R, true><<<grid, threads, smem, s>>>(a);
+  else line_warp_kernel<R, false><<<grid, threads, smem, s>>>(a);
 }
 
 static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
@@ -242,14 +156,14 @@ int line_fft_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_fft_kernel<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<10, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<12, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::line_warp_kernel<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "line kernel attributes");
 }
 

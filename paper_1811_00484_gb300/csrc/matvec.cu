@@ -46,13 +46,12 @@ int ensure_workspace(vie_op* op, int B) {
   return VIE_OK;
 }
 
-// The stages of one matvec with the caller-chosen scratch `ws` (T1 then T2).
+// Arguments of the four line stages for one operator and batch, T1 then T2 in `ws`.
 template <typename T>
-int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
-               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-               const int* active, cudaStream_t s) {
+LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B,
+                               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
+                               const int* active) {
   using C = cx<T>;
-  const bool stored = (path == VIE_PATH_UNCOMPRESSED);
   const long long n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
   const long long P1 = op->P[0], P2 = op->P[1], P3 = op->P[2];
   C* T1 = static_cast<C*>(ws);
@@ -61,12 +60,10 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   for (int q = 0; q < 3; ++q) {
     if constexpr (sizeof(T) == 4) r[q] = op->roots32[q]; else r[q] = op->roots64[q];
   }
-
-  if (!stored) VIE_TRY(launch_slab_cores<T>(op, s));
-
+  LineStages<T> st = {};
   // x stage: J -> T1
   {
-    LineArgs<T> a = {};
+    LineArgs<T>& a = st.s[0];
     a.in = in;
     a.out = T1;
     a.roots = r[0];
@@ -83,16 +80,13 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
     a.in_bs = n1 * n2 * n3; a.in_os = n3; a.in_ls = n2 * n3; a.in_cs = 1;
     a.out_bs = P1 * n2 * n3; a.out_os = n3; a.out_ls = n2 * n3; a.out_cs = 1;
     a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
-    a.batch_per_rhs = 3;
-    a.active = active;
     a.prof_family = PF_LINE_X;
     a.prof_batch_bytes = (unsigned long long)((n1 + P1) * n2 * n3 * sizeof(C)) +
                          ((a.flags & PRO_CHI) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull);
-    launch_line_fft<T>(a, s);
   }
   // y stage: T1 -> T2
   {
-    LineArgs<T> a = {};
+    LineArgs<T>& a = st.s[1];
     a.in = T1;
     a.out = T2;
     a.roots = r[1];
@@ -105,17 +99,12 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
     a.ncol = (int)n3;
     a.in_bs = P1 * n2 * n3; a.in_os = n2 * n3; a.in_ls = n3; a.in_cs = 1;
     a.out_bs = P1 * P2 * n3; a.out_os = P2 * n3; a.out_ls = n3; a.out_cs = 1;
-    a.batch_per_rhs = 3;
-    a.active = active;
     a.prof_family = PF_LINE_Y;
     a.prof_batch_bytes = (unsigned long long)((n2 + P2) * P1 * n3 * sizeof(C));
-    launch_line_fft<T>(a, s);
   }
-  // z stage fused with the rebuild and the product
-  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s));
   // inverse y stage: T2 -> T1 (crop)
   {
-    LineArgs<T> a = {};
+    LineArgs<T>& a = st.s[2];
     a.in = T2;
     a.out = T1;
     a.roots = r[1];
@@ -129,15 +118,12 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
     a.ncol = (int)n3;
     a.in_bs = P1 * P2 * n3; a.in_os = P2 * n3; a.in_ls = n3; a.in_cs = 1;
     a.out_bs = P1 * n2 * n3; a.out_os = n2 * n3; a.out_ls = n3; a.out_cs = 1;
-    a.batch_per_rhs = 3;
-    a.active = active;
     a.prof_family = PF_LINE_IY;
     a.prof_batch_bytes = (unsigned long long)((n2 + P2) * P1 * n3 * sizeof(C));
-    launch_line_fft<T>(a, s);
   }
   // inverse x stage: T1 -> out (crop, scale, epilogue)
   {
-    LineArgs<T> a = {};
+    LineArgs<T>& a = st.s[3];
     a.in = T1;
     a.out = out;
     a.roots = r[0];
@@ -155,14 +141,35 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
     a.in_bs = P1 * n2 * n3; a.in_os = n3; a.in_ls = n2 * n3; a.in_cs = 1;
     a.out_bs = n1 * n2 * n3; a.out_os = n3; a.out_ls = n2 * n3; a.out_cs = 1;
     a.chi_os = n3; a.chi_ls = n2 * n3; a.chi_cs = 1;
-    a.batch_per_rhs = 3;
-    a.active = active;
     a.prof_family = PF_LINE_IX;
     a.prof_batch_bytes = (unsigned long long)((P1 + n1) * n2 * n3 * sizeof(C)) +
                          ((a.flags & (EPI_SUB | EPI_ADD)) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull) +
                          ((a.flags & EPI_CHI) ? (unsigned long long)(n1 * n2 * n3 * sizeof(C)) : 0ull);
-    launch_line_fft<T>(a, s);
   }
+  for (int i = 0; i < 4; ++i) {
+    st.s[i].batch_per_rhs = 3;
+    st.s[i].active = active;
+    st.s[i].threads = op->tune.line_threads[i];
+  }
+  return st;
+}
+
+// The stages of one matvec with the caller-chosen scratch `ws` (T1 then T2).
+template <typename T>
+int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
+               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
+               const int* active, cudaStream_t s) {
+  using C = cx<T>;
+  const bool stored = (path == VIE_PATH_UNCOMPRESSED);
+  const LineStages<T> st = make_line_stages<T>(op, ws, in, out, B, pro_flags, epi_flags, chi,
+                                               addend, active);
+  C* T2 = const_cast<C*>(st.s[1].out);
+  if (!stored) VIE_TRY(launch_slab_cores<T>(op, s));
+  launch_line_fft<T>(st.s[0], s);
+  launch_line_fft<T>(st.s[1], s);
+  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s));
+  launch_line_fft<T>(st.s[2], s);
+  launch_line_fft<T>(st.s[3], s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "matvec launch");
   return VIE_OK;
@@ -181,6 +188,9 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
 
 template int matvec_run<float>(const vie_op*, void*, const float2*, float2*, int, int, int, int,
                                const float2*, const float2*, const int*, cudaStream_t);
+template LineStages<float> make_line_stages<float>(const vie_op*, void*, const float2*, float2*, int,
+                                                   int, int, const float2*, const float2*,
+                                                   const int*);
 template int matvec_impl<float>(const vie_op*, const float2*, float2*, int, int, int, int,
                                 const float2*, const float2*, const int*, cudaStream_t);
 template int matvec_impl<double>(const vie_op*, const double2*, double2*, int, int, int, int,

@@ -1,0 +1,262 @@
+// Several operators (grids of different sizes, each with its own batch of
+// right-hand sides) through one launch per matvec stage, and the autotuner
+// that picks the line stages' CTA size.
+//
+// Each multi-grid kernel gets a table of per-problem arguments as a kernel
+// parameter, with the prefix sums of the problems' block counts; a CTA finds
+// its problem from its block index and runs the same device body as the
+// per-operator kernel, dispatching on that problem's FFT radix R = P / 32.
+#include <algorithm>
+#include <vector>
+
+#include "stages.cuh"
+
+template <typename T> vie::SlabArgs<T> make_slab_args(const vie_op* op);
+template <typename T>
+vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool stored,
+                                  const int* active);
+
+namespace vie {
+
+constexpr int kMaxMulti = 8;
+
+struct MultiLine {
+  int count;
+  int R[kMaxMulti];
+  long long start[kMaxMulti + 1];
+  LineArgs<float> a[kMaxMulti];
+};
+struct MultiFused {
+  int count;
+  int R[kMaxMulti];
+  long long start[kMaxMulti + 1];
+  FusedArgs<float> a[kMaxMulti];
+};
+struct MultiSlab {
+  int count;
+  long long start[kMaxMulti + 1];
+  SlabArgs<float> a[kMaxMulti];
+};
+
+__device__ __forceinline__ int find_problem(const long long* start, int count, long long b) {
+  int p = 0;
+  while (p + 1 < count && b >= start[p + 1]) ++p;
+  return p;
+}
+
+// radices the multi-grid kernels carry (P = 32 R <= 256)
+__host__ __device__ constexpr bool multi_radix(int R) {
+  return R == 1 || R == 2 || R == 3 || R == 4 || R == 5 || R == 6 || R == 8;
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(256) line_multi_kernel(const __grid_constant__ MultiLine m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* smem = reinterpret_cast<float2*>(smem_raw);
+  const long long b = blockIdx.x;
+  const int p = find_problem(m.start, m.count, b);
+  const LineArgs<float>& a = m.a[p];
+  const long long t = b - m.start[p];
+  const int ntc = (a.ncol + kLineTile - 1) / kLineTile;
+  const int ct = (int)(t % ntc);
+  const int o = (int)((t / ntc) % a.nother);
+  const int bb = (int)(t / ((long long)ntc * a.nother));
+  switch (m.R[p]) {
+    case 1: line_warp_tile<1, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 2: line_warp_tile<2, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 3: line_warp_tile<3, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 4: line_warp_tile<4, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 5: line_warp_tile<5, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 6: line_warp_tile<6, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    case 8: line_warp_tile<8, HALF>(a, ct * kLineTile, o, bb, smem); break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(128) fused_multi_kernel(const __grid_constant__ MultiFused m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* smem = reinterpret_cast<float2*>(smem_raw);
+  const long long b = blockIdx.x;
+  const int p = find_problem(m.start, m.count, b);
+  const int g = (int)(b - m.start[p]);
+  switch (m.R[p]) {
+    case 1: fused_warp_group<1, false>(m.a[p], g, smem); break;
+    case 2: fused_warp_group<2, false>(m.a[p], g, smem); break;
+    case 3: fused_warp_group<3, false>(m.a[p], g, smem); break;
+    case 4: fused_warp_group<4, false>(m.a[p], g, smem); break;
+    case 5: fused_warp_group<5, false>(m.a[p], g, smem); break;
+    case 6: fused_warp_group<6, false>(m.a[p], g, smem); break;
+    case 8: fused_warp_group<8, false>(m.a[p], g, smem); break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(256) slab_multi_kernel(const __grid_constant__ MultiSlab m) {
+  const long long b = blockIdx.x;
+  const int p = find_problem(m.start, m.count, b);
+  const int local = (int)(b - m.start[p]);
+  slab_core_block<float>(m.a[p], local / 6, local % 6);
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+static bool multi_eligible(const vie_op* op) {
+  for (int q = 0; q < 3; ++q)
+    if (op->P[q] % 32 != 0 || !multi_radix(op->P[q] / 32)) return false;
+  return true;
+}
+
+int multi_init_attributes() {
+  const int lim = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(line_multi_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(line_multi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "multi kernel attributes");
+}
+
+// One launch per stage for up to kMaxMulti operators.
+static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, float2* const* Y,
+                              const int* B, int count, cudaStream_t s) {
+  std::vector<LineStages<float>> lines(count);
+  MultiLine ml[4];
+  MultiFused mf;
+  MultiSlab ms;
+  size_t smem_line = 0, smem_fused = 0;
+  for (int st = 0; st < 4; ++st) ml[st].count = count;
+  mf.count = ms.count = count;
+  long long lstart[4] = {0, 0, 0, 0}, fstart = 0, sstart = 0;
+  for (int p = 0; p < count; ++p) {
+    const vie_op* op = ops[p];
+    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B[p]));
+    lines[p] = make_line_stages<float>(op, op->ws.ptr, J[p], Y[p], B[p], 0, 0, nullptr, nullptr,
+                                       nullptr);
+    for (int st = 0; st < 4; ++st) {
+      LineArgs<float> a = lines[p].s[st];
+      a.prof = prof_bytes(a.prof_family);
+      ml[st].a[p] = a;
+      ml[st].R[p] = a.plan.N / 32;
+      ml[st].start[p] = lstart[st];
+      lstart[st] += (long long)((a.ncol + kLineTile - 1) / kLineTile) * a.nother * a.nbatch;
+      smem_line = std::max(smem_line, line_warp_smem(a.plan.N / 32));
+    }
+    float2* T2 = lines[p].s[1].out;
+    mf.a[p] = make_fused_args<float>(op, T2, B[p], false, nullptr);
+    mf.R[p] = op->P[2] / 32;
+    mf.start[p] = fstart;
+    fstart += (long long)op->H[0] * op->H[1];
+    smem_fused = std::max(smem_fused, fused_warp_smem(op->P[2] / 32, op->H[2], op->rmax[2]));
+    ms.a[p] = make_slab_args<float>(op);
+    ms.start[p] = sstart;
+    sstart += (long long)op->H[0] * 6;
+  }
+  for (int st = 0; st < 4; ++st) ml[st].start[count] = lstart[st];
+  mf.start[count] = fstart;
+  ms.start[count] = sstart;
+  static const int fam[4] = {PF_LINE_X, PF_LINE_Y, PF_LINE_IY, PF_LINE_IX};
+  {
+    ProfScope ps(PF_SLAB, s);
+    slab_multi_kernel<<<(unsigned)sstart, 256, 0, s>>>(ms);
+  }
+  for (int st = 0; st < 4; ++st) {
+    if (st == 2) {
+      ProfScope ps(PF_FUSED_TUCKER, s);
+      fused_multi_kernel<<<(unsigned)fstart, 128, smem_fused, s>>>(mf);
+    }
+    ProfScope ps(fam[st], s);
+    // every stage of every operator is a half-length transform (zero pad or crop)
+    line_multi_kernel<true><<<(unsigned)lstart[st], 256, smem_line, s>>>(ml[st]);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "multi-grid matvec launch");
+  return VIE_OK;
+}
+
+extern "C" int vie_matvec_multi(const vie_op* const* ops, const void* const* J, void* const* Y,
+                                const int* B, int count, void* stream) {
+  if (!ops || !J || !Y || !B || count < 1) {
+    set_error("NULL argument or empty problem list");
+    return VIE_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool all = true;
+  for (int p = 0; p < count; ++p) {
+    if (!ops[p] || !J[p] || !Y[p] || B[p] < 1 || B[p] > 4096) {
+      set_error("problem %d: NULL operator/array or batch outside [1, 4096]", p);
+      return VIE_ERR_ARG;
+    }
+    all = all && multi_eligible(ops[p]);
+  }
+  if (!all) {
+    // a grid edge that is not 32 R (R <= 8): one matvec per operator
+    for (int p = 0; p < count; ++p)
+      VIE_TRY(matvec_impl<float>(ops[p], static_cast<const float2*>(J[p]), static_cast<float2*>(Y[p]),
+                                 B[p], VIE_PATH_TUCKER, 0, 0, nullptr, nullptr, nullptr, s));
+    return VIE_OK;
+  }
+  for (int p0 = 0; p0 < count; p0 += kMaxMulti) {
+    const int c = std::min(kMaxMulti, count - p0);
+    VIE_TRY(matvec_multi_chunk(ops + p0, reinterpret_cast<const float2* const*>(J) + p0,
+                               reinterpret_cast<float2* const*>(Y) + p0, B + p0, c, s));
+  }
+  return VIE_OK;
+}
+
+// Time the FP32 Tucker matvec at batch B with each candidate CTA size of each
+// line stage (the other stages at their current choice) and keep the fastest.
+extern "C" int vie_autotune(vie_op* op, int B, void* stream) {
+  if (!op || B < 1 || B > 4096) {
+    set_error("bad operator or batch");
+    return VIE_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  VIE_TRY(ensure_workspace(op, B));
+  const size_t n = (size_t)B * 3 * op->n[0] * op->n[1] * op->n[2];
+  float2 *J = nullptr, *Y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = VIE_OK;
+  if (cudaMalloc(&J, n * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&Y, n * sizeof(float2)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("autotune scratch allocation failed");
+    rc = VIE_ERR_OOM;
+  }
+  if (rc == VIE_OK) {
+    cudaMemsetAsync(J, 0, n * sizeof(float2), s);
+    static const int cand[3] = {64, 128, 256};
+    for (int st = 0; st < 4 && rc == VIE_OK; ++st) {
+      float best = 1e30f;
+      int best_t = op->tune.line_threads[st];
+      for (int t : cand) {
+        op->tune.line_threads[st] = t;
+        float total = 0.f;
+        for (int rep = 0; rep < 4 && rc == VIE_OK; ++rep) {   // rep 0 warms up
+          cudaEventRecord(e0, s);
+          rc = matvec_impl<float>(op, J, Y, B, VIE_PATH_TUCKER, 0, 0, nullptr, nullptr, nullptr, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) total += ms;
+        }
+        if (total < best) {
+          best = total;
+          best_t = t;
+        }
+      }
+      op->tune.line_threads[st] = best_t;
+    }
+    op->tune.tuned_batch = B;
+  }
+  cudaFree(J);
+  cudaFree(Y);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}

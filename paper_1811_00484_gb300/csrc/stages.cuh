@@ -1,0 +1,281 @@
+// Device bodies of the register-path (N = 32 R) matvec stages, shared by the
+// per-operator kernels (lines.cu, fused.cu) and the multi-grid kernels
+// (multi.cu): one x/y line tile, one fused z-line group, one slab-core block.
+#pragma once
+
+#include "warpfft.cuh"
+
+namespace vie {
+
+// sign of component c (xx, xy, xz, yy, yz, zz) under k_q -> P_q - k_q: the
+// dyad (k0^2 delta_ab + d_a d_b) g is odd in coordinate q once per index equal to q
+__device__ __forceinline__ int parity_sign(int c, int axis) {
+  const int a = c < 3 ? 0 : (c < 5 ? 1 : 2);
+  const int b = c == 0 ? 0 : (c == 1 || c == 3) ? 1 : 2;
+  return (((a == axis) + (b == axis)) & 1) ? -1 : 1;
+}
+
+template <typename T> struct SlabArgs {
+  const cx<T>* core[6];
+  const cx<T>* U1[6];
+  int r1[6], r2[6], r3[6];
+  cx<T>* slab;
+  long long slab_stride;
+  int r2max, r3max;
+  unsigned long long* prof;
+  unsigned long long prof_launch_bytes;
+};
+
+template <typename T> struct FusedArgs {
+  cx<T>* data;                 // [B*3][P1][P2][n3], transformed in place
+  const cx<T>* roots;          // P3-th roots of unity
+  FftPlan plan;
+  int n3, P1, P2, P3, H1, H2, H3;
+  int B;
+  long long comp_stride;       // P1 * P2 * n3
+  const CompMeta<T>* meta;     // [6] (Tucker)
+  int r2max, r3max;
+  const cx<T>* spec;           // [6][P1][P2][P3] (stored)
+  long long spec_stride;       // P1 * P2 * P3
+  const int* active;           // per RHS, nullptr = all
+  int lines_per_round;         // z-lines (x3 components) held in shared memory at once
+  int ld;                      // shared-memory line stride
+  unsigned long long* prof;    // profiler byte counter (nullptr = off)
+  unsigned long long prof_rhs_bytes, prof_launch_bytes;
+};
+
+// S_c[k1] = core_c x1 U1_c[k1, :] for one (k1, c): the first stage of eq. (13)
+template <typename T>
+__device__ __forceinline__ void slab_core_block(const SlabArgs<T>& a, int k1, int c) {
+  using C = cx<T>;
+  const int r1 = a.r1[c], r2 = a.r2[c], r3 = a.r3[c];
+  const C* core = a.core[c];
+  const C* u1 = a.U1[c] + (long long)k1 * r1;
+  C* S = a.slab + c * a.slab_stride + (long long)k1 * a.r2max * a.r3max;
+  for (int it = threadIdx.x; it < r2 * r3; it += blockDim.x) {
+    const int b = it / r3, g = it % r3;
+    C acc = czero<C>();
+    for (int al = 0; al < r1; ++al) acc = cmadd(u1[al], core[(al * r2 + b) * r3 + g], acc);
+    S[b * a.r3max + g] = acc;
+  }
+}
+
+// Tile slot of element (row p, column c): rows of 16 columns with the
+// column index XOR-swizzled by (p ^ p>>4 ^ p>>6) mod 16.  Row-wise loads and
+// stores stay conflict-free (a permutation within the row), and so do the
+// warps' column accesses at natural rows lane + 32 j and at bit-reversed rows
+// k1 + R brev5(lane) for every power-of-two R (at most 3-way otherwise).
+__device__ __forceinline__ int tile_slot(int p, int c) {
+  return p * 16 + (c ^ ((p ^ (p >> 4) ^ (p >> 6)) & 15));
+}
+
+constexpr int kLineTile = 16;      // columns per line tile
+
+__host__ __device__ constexpr size_t line_warp_smem(int R) {
+  return (size_t)(32 * R * kLineTile + 32 * R) * sizeof(float2);
+}
+
+// One tile of 16 contiguous columns of strided lines (an x or y stage), for
+// batch index bb and outer index o.  The CTA stages the tile in shared
+// memory (coalesced rows), each warp pulls whole columns into registers,
+// transforms them with the lane FFT and writes them back; forward transforms
+// write the bit-reversed lane layout to natural rows, inverse transforms read
+// it from natural rows.  HALF: forward from N/2 loaded points, or inverse
+// cropped to N/2 stored points.  Every thread of the block must call it.
+template <int R, bool HALF>
+__device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0, int o, int bb,
+                                               float2* smem) {
+  using C = float2;
+  constexpr int N = 32 * R;
+  constexpr int TW = kLineTile;
+  C* tile = smem;                  // element (row p, column c) at tile_slot(p, c)
+  C* roots = smem + N * TW;
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  if (a.prof != nullptr && c0 == 0 && o == 0 && tid == 0) atomicAdd(a.prof, a.prof_batch_bytes);
+  const int ncols = min(TW, a.ncol - c0);
+
+  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
+  for (int e = tid; e < a.lin * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c < ncols) {
+      C v = in[p * a.in_ls + c];
+      if (a.flags & PRO_CONJ) v = conjg(v);
+      if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      tile[tile_slot(p, c)] = v;
+    }
+  }
+  __syncthreads();
+
+  const int br = brev5(lane);
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, roots, N);
+  for (int c = warp; c < ncols; c += nwarp) {
+    C v[R];
+    if (!a.inverse) {
+#pragma unroll
+      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
+        const int p = lane + 32 * j;
+        v[j] = p < a.lin ? tile[tile_slot(p, c)] : make_float2(0.f, 0.f);
+      }
+      warp_fft_fwd<C, float, R, HALF>(v, lc, roots, N);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const int p = k1 + R * br;
+        if (p < a.lout) tile[tile_slot(p, c)] = v[k1];
+      }
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) v[k1] = tile[tile_slot(k1 + R * br, c)];
+      warp_fft_inv<C, float, R, HALF>(v, lane, lc, roots, N);
+#pragma unroll
+      for (int j = 0; j < (HALF ? (R + 1) / 2 : R); ++j) {
+        const int p = lane + 32 * j;
+        if (p < a.lout) tile[tile_slot(p, c)] = v[j];
+      }
+    }
+  }
+  __syncthreads();
+
+  const long long obase = bb * a.out_bs + o * a.out_os + (long long)c0;
+  C* out = a.out + obase;
+  for (int e = tid; e < a.lout * TW; e += nth) {
+    const int c = e % TW, p = e / TW;
+    if (c >= ncols) continue;
+    C v = a.scale * tile[tile_slot(p, c)];
+    if (a.flags & EPI_CONJ) v = conjg(v);
+    const long long oi = p * a.out_ls + c;
+    if (a.flags & (EPI_SUB | EPI_ADD)) {
+      if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
+      const C w = a.addend[obase + oi];
+      v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
+    }
+    out[oi] = v;
+  }
+}
+
+// Slot of z-frequency k in a row of the rebuilt half fibre: one padding slot
+// every 8 entries, so the lanes' folded, bit-reversed frequencies (stride R)
+// fall in different banks (at most 2-way for the radices used, 4-way at R=10).
+__device__ __forceinline__ int ghalf_slot(int k) { return k + (k >> 3); }
+
+__host__ __device__ constexpr size_t fused_warp_smem(int R, int H3, int r3max) {
+  return (size_t)(32 * R + 6 * ((H3 - 1) + ((H3 - 1) >> 3) + 1) + 6 * r3max) * sizeof(float2);
+}
+
+// One (k1, k2) mirror group of the fused stage on the register path (P3 = 32 R):
+// the four warps of the CTA take one mirror z-line each, hold the three
+// components of every right-hand side in registers, and do the forward lane
+// FFT, the voxel-wise product with the rebuilt (or stored) components in the
+// bit-reversed lane layout, and the inverse lane FFT.  The rebuild of the
+// half fibre (k3 <= P3/2) is shared by the CTA.  Every thread must call it.
+template <int R, bool STORED>
+__device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int g, float2* smem) {
+  using C = float2;
+  constexpr int P3 = 32 * R;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int n3 = a.n3, H3 = a.H3;
+  const int k1 = g / a.H2, k2 = g % a.H2;
+  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
+  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
+  const int nl = nx * ny;
+  if (a.prof != nullptr && g == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
+
+  const int GS = ghalf_slot(H3 - 1) + 1;   // padded row length of the half fibre
+  C* roots = smem;
+  C* ghalf = roots + P3;               // [6][GS]
+  C* wv = ghalf + 6 * GS;              // [6][r3max]
+  for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
+  if (!STORED) {
+    for (int it = tid; it < 6 * a.r3max; it += nth) {
+      const int c = it / a.r3max, gm = it % a.r3max;
+      const CompMeta<float> m = a.meta[c];
+      C acc = make_float2(0.f, 0.f);
+      if (gm < m.r3) {
+        const C* S = m.slab + (long long)k1 * a.r2max * a.r3max;
+        const C* u2 = m.U2 + (long long)k2 * m.r2;
+        for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max + gm], acc);
+      }
+      wv[it] = acc;
+    }
+    __syncthreads();
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it % H3;
+      const CompMeta<float> m = a.meta[c];
+      const C* u3 = m.U3 + (long long)kk * m.r3;
+      const C* w = wv + c * a.r3max;
+      C acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
+      ghalf[c * GS + ghalf_slot(kk)] = acc;
+    }
+  }
+  __syncthreads();
+  if (warp >= nl) return;                  // no block barrier follows
+
+  const int ix = warp / ny, iy = warp % ny;
+  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
+  const int br = brev5(lane);
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, roots, P3);
+  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
+  for (int b = 0; b < a.B; ++b) {
+    if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
+    C v[3][R];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < (R + 1) / 2; ++j) {
+        const int p = lane + 32 * j;
+        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+      }
+      warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int kk = q + R * br;                       // z-frequency held in register q
+      C gc[6];
+      if (STORED) {
+        const long long off = ((long long)kx * a.P2 + ky) * P3 + kk;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) gc[c] = a.spec[c * a.spec_stride + off];
+      } else {
+        const bool zm = 2 * kk > P3;
+        const int fold = zm ? P3 - kk : kk;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          int s = 1;
+          if (ix) s *= parity_sign(c, 0);
+          if (iy) s *= parity_sign(c, 1);
+          if (zm) s *= parity_sign(c, 2);
+          const C gv = ghalf[c * GS + ghalf_slot(fold)];
+          gc[c] = (s > 0) ? gv : make_float2(-gv.x, -gv.y);
+        }
+      }
+      const C jx = v[0][q], jy = v[1][q], jz = v[2][q];
+      // Y_a = sum_b G_ab J_b with G symmetric: xx xy xz / xy yy yz / xz yz zz
+      v[0][q] = gc[0] * jx + gc[1] * jy + gc[2] * jz;
+      v[1][q] = gc[1] * jx + gc[3] * jy + gc[4] * jz;
+      v[2][q] = gc[2] * jx + gc[4] * jy + gc[5] * jz;
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      warp_fft_inv<C, float, R, true>(v[comp], lane, lc, roots, P3);
+      C* dst = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < (R + 1) / 2; ++j) {
+        const int p = lane + 32 * j;
+        if (p < n3) dst[p] = v[comp][j];
+      }
+    }
+  }
+}
+
+}  // namespace vie

@@ -114,6 +114,7 @@ template <typename T> struct LineArgs {
   long long chi_os, chi_ls, chi_cs;    // chi index = o*chi_os + p*chi_ls + c*chi_cs
   int batch_per_rhs;                   // batches per RHS (3 components) for `active`
   const int* active;                   // per-RHS flag (nullptr = all active)
+  int threads;                         // CTA size of the register-path kernel (0 = 256)
   int prof_family;                     // profiler family of this launch
   unsigned long long* prof;            // profiler byte counter (nullptr = off)
   unsigned long long prof_batch_bytes; // algorithmic bytes per active batch index
@@ -137,6 +138,12 @@ struct Workspace {
   size_t bytes = 0;
 };
 
+// Launch shapes chosen by vie_autotune (defaults until it runs).
+struct Tuning {
+  int line_threads[4] = {256, 256, 256, 256};   // x, y, inverse y, inverse x stages
+  int tuned_batch = 0;                          // batch the choice was timed at (0 = default)
+};
+
 struct vie_op {
   vie_grid grid;
   int n[3], P[3], H[3];
@@ -155,6 +162,7 @@ struct vie_op {
   void* meta = nullptr;
   Workspace ws;
   int ws_batch = 0;
+  Tuning tune;
   // solver scratch
   Workspace solve_ws;
   void* solver = nullptr;    // cached solver state (graphs), see solve.cu
@@ -196,6 +204,14 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
                 cudaStream_t s);
 int ensure_workspace(vie_op* op, int B);
+// The four line-stage launches of one matvec (x, y, inverse y, inverse x).
+template <typename T> struct LineStages {
+  LineArgs<T> s[4];
+};
+template <typename T>
+LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B,
+                               int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
+                               const int* active);
 // the same stages with an explicit scratch buffer of at least matvec_scratch_bytes() bytes
 template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
@@ -213,6 +229,7 @@ int line_fft_init_attributes();
 // dynamic shared memory: resident CTAs per SM x SMs, capped by `work`
 int persistent_grid(const void* kernel, int threads, size_t smem, long long work);
 int fused_init_attributes();
+int multi_init_attributes();
 
 // solver (solve.cu)
 int solve_impl(const vie_op* op, const void* chi, const void* rhs, void* w, int B, int flags,

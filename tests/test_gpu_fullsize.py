@@ -6,8 +6,10 @@ outputs one by one: the BTTB sum at a sampled voxel m is
 with T from oracle.kernel (dyadic kernel times h^3, self term at m' = m).
 Properties that hold at any size cover the rest (residuals of the GPU's own
 FP64 operator, finite differences of the loss).
-Tolerances: sampled FP32 matvec outputs are compared relative to the RMS of
-the whole output (1e-5 plus the HOSVD truncation tolerance); FP64 ones to 1e-9.
+Tolerances: sampled matvec outputs are compared relative to the RMS of the
+whole output, against the exact (uncompressed) oracle sum: 1e-5 (the FP32
+matvec gate) plus four times the HOSVD tolerance, because the truncation
+error is not spread evenly over the voxels.
 """
 import numpy as np
 import pytest
