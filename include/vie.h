@@ -103,6 +103,9 @@ typedef struct vie_op_info_t {
     int ranks[6][3];             /* multilinear ranks per component (xx..zz)   */
     size_t tucker_bytes;         /* c64 cores + factors as stored (half rows)   */
     size_t tucker_bytes_full;    /* c64 cores + full factors (P_q rows), eq. (13)*/
+    size_t slab_bytes;           /* c64 slab cores core x1 U1[k1,:] for the
+                                    P1/2+1 rows k1 (formed at setup, reused by
+                                    every matvec)                               */
     size_t uncompressed_bytes;   /* six c64 spectra, 6 P1 P2 P3 x 8 bytes       */
     size_t workspace_bytes;      /* scratch currently held                      */
     int has_uncompressed;        /* VIE_STORE_UNCOMPRESSED was given            */
@@ -180,8 +183,9 @@ int vie_reserve(vie_op* op, int max_batch);
 /*
  * Y = G J for B >= 1 vector fields (Section V.B): zero-pad, 3-D FFT, voxel-
  * wise product with the six components (rebuilt from the Tucker form, eq.
- * (13), or read from the stored spectra for VIE_PATH_UNCOMPRESSED), inverse
- * FFT, crop.  J, Y: device [B][3][n1][n2][n3] in `precision`; Y may alias J.
+ * (13) — the last two mode products on chip at every call, from slab cores
+ * core x1 U1[k1,:] formed at setup — or read from the stored spectra for
+ * VIE_PATH_UNCOMPRESSED), inverse FFT, crop.  J, Y: device [B][3][n1][n2][n3] in `precision`; Y may alias J.
  */
 int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
                int precision, void* stream);
@@ -202,7 +206,7 @@ int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
  * needs to start at zero: every call overwrites what it reads.
  * The first call on each device looks up the scratch address (with that
  * device current); make that first call before any stream capture.
- * All calls share the one array, and the operator's slab-core buffer, so
+ * All calls share the one array, so
  * calls that overlap on the GPU (different streams, or concurrent host
  * threads) race; serialise them.  J, Y: device [B][3][n1][n2][n3] c64.
  */
@@ -213,8 +217,7 @@ int vie_matvec_noalloc(const vie_op* op, const void* J, void* Y, int B,
  * Y_p = G_p J_p for `count` operators at once, c64, Tucker path: the batched
  * and mixed-size counterpart of vie_matvec (Section V.B for each operator).
  * Grids of different sizes, each with its own batch B[p], go through one
- * launch per stage (slab cores, x, y, fused z/rebuild/product, inverse y,
- * inverse x) when every padded edge 2 n_q is 32 R with R in {1..6, 8};
+ * launch per stage (x, y, fused z/rebuild/product, inverse y, inverse x) when every padded edge 2 n_q is 32 R with R in {1..6, 8};
  * otherwise (or for count > 8, in groups of 8) through the per-operator path.
  * ops, J, Y, B: host arrays of `count` entries; J[p], Y[p]: device
  * [B[p]][3][n1][n2][n3] of operator p.  Operators must be distinct (each

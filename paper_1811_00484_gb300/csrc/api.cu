@@ -167,6 +167,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   }
   r.tucker_bytes = half * sizeof(float2);
   r.tucker_bytes_full = fullf * sizeof(float2);
+  r.slab_bytes = 6 * op->slab_stride * sizeof(float2);
   r.uncompressed_bytes = 6ull * op->P[0] * op->P[1] * op->P[2] * sizeof(float2);
   r.workspace_bytes = op->ws.bytes + op->solve_ws.bytes;
   r.has_uncompressed = op->spec32 != nullptr;

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> 
 
 template <int R, bool STORED>
 static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
-  const size_t smem = fused_warp_smem(R, a.H3, a.r3max);
+  const size_t smem = fused_warp_smem(R, a.H3, a.r2max, a.r3max);
   const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
   a.prof = prof_bytes(fam);
   a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);

@@ -31,6 +31,9 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
   const int ncols = min(TW, a.ncol - c0);
 
   for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  const T rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                   ? (T)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                   : (T)1;
 
   const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0 * a.in_cs;
   const bool col_fast_in = (a.in_cs == 1);
@@ -40,6 +43,7 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
     C v = czero<C>();
     if (p < a.lin && c < ncols) {
       v = in[p * a.in_ls + c * a.in_cs];
+      if (a.flags & PRO_RSCALE) v = rs * v;
       if (a.flags & PRO_CONJ) v = conjg(v);
       if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c) * a.chi_cs] * v;
     }
@@ -61,7 +65,8 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
     const long long oi = p * a.out_ls + c * a.out_cs;
     if (a.flags & (EPI_SUB | EPI_ADD)) {
       if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c) * a.chi_cs] * v;
-      const C w = a.addend[obase + oi];
+      C w = a.addend[obase + oi];
+      if (a.flags & EPI_RSCALE) w = rs * w;
       v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
     }
     out[oi] = v;

@@ -13,7 +13,6 @@
 // runs n2 n3 lines, the y stage P1 n3 lines.
 #include "vie_internal.cuh"
 
-template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
                  cudaStream_t s);
@@ -50,7 +49,7 @@ int ensure_workspace(vie_op* op, int B) {
 template <typename T>
 LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B,
                                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-                               const int* active) {
+                               const int* active, const double* rscale, long long rscale_stride) {
   using C = cx<T>;
   const long long n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
   const long long P1 = op->P[0], P2 = op->P[1], P3 = op->P[2];
@@ -74,6 +73,7 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
     a.inverse = 0;
     a.scale = (T)1;
     a.flags = pro_flags & (PRO_CONJ | PRO_CHI);
+    if (rscale) a.flags |= PRO_RSCALE;
     a.nbatch = 3 * B;
     a.nother = (int)n2;
     a.ncol = (int)n3;
@@ -135,6 +135,7 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
     a.inverse = 1;
     a.scale = (T)(1.0 / ((double)P1 * (double)P2 * (double)P3));
     a.flags = epi_flags & (EPI_CONJ | EPI_SUB | EPI_ADD | EPI_CHI);
+    if (rscale && (a.flags & (EPI_SUB | EPI_ADD))) a.flags |= EPI_RSCALE;
     a.nbatch = 3 * B;
     a.nother = (int)n2;
     a.ncol = (int)n3;
@@ -150,6 +151,8 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
     st.s[i].batch_per_rhs = 3;
     st.s[i].active = active;
     st.s[i].threads = op->tune.line_threads[i];
+    st.s[i].rscale = rscale;
+    st.s[i].rscale_stride = rscale_stride;
   }
   return st;
 }
@@ -158,13 +161,12 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
 template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-               const int* active, cudaStream_t s) {
+               const int* active, cudaStream_t s, const double* rscale, long long rscale_stride) {
   using C = cx<T>;
   const bool stored = (path == VIE_PATH_UNCOMPRESSED);
   const LineStages<T> st = make_line_stages<T>(op, ws, in, out, B, pro_flags, epi_flags, chi,
-                                               addend, active);
+                                               addend, active, rscale, rscale_stride);
   C* T2 = const_cast<C*>(st.s[1].out);
-  if (!stored) VIE_TRY(launch_slab_cores<T>(op, s));
   launch_line_fft<T>(st.s[0], s);
   launch_line_fft<T>(st.s[1], s);
   VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s));
@@ -178,20 +180,23 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
-                cudaStream_t s) {
+                cudaStream_t s, const double* rscale, long long rscale_stride) {
   if (workspace_bytes_for(op, B) > op->ws.bytes) {
     VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
   }
   return matvec_run<T>(op, op->ws.ptr, in, out, B, path, pro_flags, epi_flags, chi, addend, active,
-                       s);
+                       s, rscale, rscale_stride);
 }
 
 template int matvec_run<float>(const vie_op*, void*, const float2*, float2*, int, int, int, int,
-                               const float2*, const float2*, const int*, cudaStream_t);
+                               const float2*, const float2*, const int*, cudaStream_t,
+                               const double*, long long);
 template LineStages<float> make_line_stages<float>(const vie_op*, void*, const float2*, float2*, int,
                                                    int, int, const float2*, const float2*,
-                                                   const int*);
+                                                   const int*, const double*, long long);
 template int matvec_impl<float>(const vie_op*, const float2*, float2*, int, int, int, int,
-                                const float2*, const float2*, const int*, cudaStream_t);
+                                const float2*, const float2*, const int*, cudaStream_t,
+                                const double*, long long);
 template int matvec_impl<double>(const vie_op*, const double2*, double2*, int, int, int, int,
-                                 const double2*, const double2*, const int*, cudaStream_t);
+                                 const double2*, const double2*, const int*, cudaStream_t,
+                                 const double*, long long);

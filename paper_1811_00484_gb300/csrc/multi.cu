@@ -11,7 +11,6 @@
 
 #include "stages.cuh"
 
-template <typename T> vie::SlabArgs<T> make_slab_args(const vie_op* op);
 template <typename T>
 vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool stored,
                                   const int* active);
@@ -31,11 +30,6 @@ struct MultiFused {
   int R[kMaxMulti];
   long long start[kMaxMulti + 1];
   FusedArgs<float> a[kMaxMulti];
-};
-struct MultiSlab {
-  int count;
-  long long start[kMaxMulti + 1];
-  SlabArgs<float> a[kMaxMulti];
 };
 
 __device__ __forceinline__ int find_problem(const long long* start, int count, long long b) {
@@ -91,13 +85,6 @@ __global__ void __launch_bounds__(128) fused_multi_kernel(const __grid_constant_
   }
 }
 
-__global__ void __launch_bounds__(256) slab_multi_kernel(const __grid_constant__ MultiSlab m) {
-  const long long b = blockIdx.x;
-  const int p = find_problem(m.start, m.count, b);
-  const int local = (int)(b - m.start[p]);
-  slab_core_block<float>(m.a[p], local / 6, local % 6);
-}
-
 }  // namespace vie
 
 using namespace vie;
@@ -126,11 +113,10 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
   std::vector<LineStages<float>> lines(count);
   MultiLine ml[4];
   MultiFused mf;
-  MultiSlab ms;
   size_t smem_line = 0, smem_fused = 0;
   for (int st = 0; st < 4; ++st) ml[st].count = count;
-  mf.count = ms.count = count;
-  long long lstart[4] = {0, 0, 0, 0}, fstart = 0, sstart = 0;
+  mf.count = count;
+  long long lstart[4] = {0, 0, 0, 0}, fstart = 0;
   for (int p = 0; p < count; ++p) {
     const vie_op* op = ops[p];
     VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B[p]));
@@ -150,19 +136,11 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
     mf.R[p] = op->P[2] / 32;
     mf.start[p] = fstart;
     fstart += (long long)op->H[0] * op->H[1];
-    smem_fused = std::max(smem_fused, fused_warp_smem(op->P[2] / 32, op->H[2], op->rmax[2]));
-    ms.a[p] = make_slab_args<float>(op);
-    ms.start[p] = sstart;
-    sstart += (long long)op->H[0] * 6;
+    smem_fused = std::max(smem_fused, fused_warp_smem(op->P[2] / 32, op->H[2], op->rmax[1], op->rmax[2]));
   }
   for (int st = 0; st < 4; ++st) ml[st].start[count] = lstart[st];
   mf.start[count] = fstart;
-  ms.start[count] = sstart;
   static const int fam[4] = {PF_LINE_X, PF_LINE_Y, PF_LINE_IY, PF_LINE_IX};
-  {
-    ProfScope ps(PF_SLAB, s);
-    slab_multi_kernel<<<(unsigned)sstart, 256, 0, s>>>(ms);
-  }
   for (int st = 0; st < 4; ++st) {
     if (st == 2) {
       ProfScope ps(PF_FUSED_TUCKER, s);

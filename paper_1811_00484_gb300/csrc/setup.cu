@@ -596,6 +596,11 @@ static int finish_operator(vie_op* op) {
   VIE_CUDA(cudaMemcpy(op->meta, m32, sizeof(m32), cudaMemcpyHostToDevice));
   VIE_CUDA(cudaMemcpy(static_cast<char*>(op->meta) + sizeof(m32), m64, sizeof(m64),
                       cudaMemcpyHostToDevice));
+  // slab cores S_c[k1] = core_c x1 U1_c[k1, :]: the first stage of eq. (13), fixed
+  // for the operator, so formed once here rather than at every matvec
+  VIE_TRY(launch_slab_cores<float>(op, 0));
+  VIE_TRY(launch_slab_cores<double>(op, 0));
+  VIE_CUDA(cudaDeviceSynchronize());
   return VIE_OK;
 }
 

@@ -5,13 +5,13 @@
 //   ||r_b|| / ||b_b|| <= tol for every right-hand side b; otherwise solve
 //   A d = r / ||r|| with FP32 GMRES and update x += ||r|| d.
 // Inner loop (FP32 vectors): restarted GMRES(m), B right-hand sides at once.
-//   Arnoldi by classical Gram-Schmidt applied twice (CGS2) with FP64 dot
-//   products, FP64 Hessenberg matrix and complex Givens rotations, FP64
-//   triangular solve.  Each restart cycle (m Arnoldi steps, the update of the
-//   iterate and the next cycle's true residual) is one CUDA graph: kernels
-//   read their state (active flags, iteration counts) from device memory,
-//   so converged right-hand sides drop out without host synchronisation;
-//   the host synchronises once per cycle.
+//   Arnoldi by classical Gram-Schmidt (one pass, or a second pass where the
+//   DGKS test asks for it) with FP32 products and FP64 sums, FP64 Hessenberg
+//   matrix and complex Givens rotations, FP64 triangular solve.  Each restart
+//   cycle (m Arnoldi steps, the update of the iterate and the next cycle's
+//   true residual) is one CUDA graph: kernels read their state (active flags,
+//   iteration counts) from device memory, so converged right-hand sides drop
+//   out without host synchronisation; the host synchronises once per cycle.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,12 +33,43 @@ __device__ __forceinline__ double2 wsum(double2 v) {
   return v;
 }
 
-// partial[b][i][chunk] = sum over the chunk of conj(V_i[b]) w[b], i = 0..k.
-// Eight basis vectors are read per step (their loads are all in flight at
-// once), each thread forms its kPer products in FP32 (the data are FP32) and
-// the warp sums them in FP32; sums across warps and chunks are FP64 (GB300's
-// FP64 rate is far below its FP32 rate, so FP64 stays out of per-element work).
-constexpr int kDotBlock = 8;
+// Krylov basis storage.  Basis vector j of right-hand side b is kept
+// unnormalised, V_j = sig[b][j] * Vraw_j, with sig[b][j] = 1 / h_{j,j-1}
+// (1 / beta for j = 0): the matvec writes A V_k straight into slot k+1 (its
+// x-stage prologue applies sig[b][k] to the input and its epilogue to the
+// subtracted input), Gram-Schmidt orthogonalises slot k+1 in place, and the
+// factor of every basis vector is folded into the coefficients that read it.
+// No pass over the data only to normalise a vector.
+//
+// The two long kernels of a Gram-Schmidt pass read the basis with 16-byte
+// loads (two complex values) when every vector starts on a 16-byte boundary
+// (N even), with several basis vectors' loads in flight per thread.
+template <int W> struct Pack { float2 c[W]; };
+
+template <int W> __device__ __forceinline__ Pack<W> ldp(const float2* p);
+template <> __device__ __forceinline__ Pack<1> ldp<1>(const float2* p) {
+  Pack<1> r;
+  r.c[0] = *p;
+  return r;
+}
+template <> __device__ __forceinline__ Pack<2> ldp<2>(const float2* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  Pack<2> r;
+  r.c[0] = make_float2(v.x, v.y);
+  r.c[1] = make_float2(v.z, v.w);
+  return r;
+}
+template <int W> __device__ __forceinline__ void stp(float2* p, const Pack<W>& v);
+template <> __device__ __forceinline__ void stp<1>(float2* p, const Pack<1>& v) { *p = v.c[0]; }
+template <> __device__ __forceinline__ void stp<2>(float2* p, const Pack<2>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.c[0].x, v.c[0].y, v.c[1].x, v.c[1].y);
+}
+template <int W> __device__ __forceinline__ Pack<W> zpack() {
+  Pack<W> r;
+#pragma unroll
+  for (int j = 0; j < W; ++j) r.c[j] = make_float2(0.f, 0.f);
+  return r;
+}
 
 __device__ __forceinline__ float2 wsum32(float2 v) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -48,116 +79,280 @@ __device__ __forceinline__ float2 wsum32(float2 v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kThreads) dots_kernel(const float2* __restrict__ V,
-                                                        const float2* __restrict__ w, int k, int B,
-                                                        long long N, int nchunk, double2* partial,
-                                                        const int* active, unsigned long long* prof,
-                                                        unsigned long long prof_bytes) {
-  const int b = blockIdx.y, chunk = blockIdx.x;
+// dots: a tile is kDotThreads x kDotPacks packs; basis vectors kDotBlock at a time
+constexpr int kDotThreads = 128;
+constexpr int kDotPacks = 2;
+constexpr int kDotBlock = 4;
+constexpr int kMaxDotCtas = 1024;             // per right-hand side (bounds the partials)
+// update: one pack per thread, basis vectors kUpdBlock at a time
+constexpr int kUpdThreads = 256;
+constexpr int kUpdBlock = 4;
+
+// partial[b][i][cta] = sum over the CTA's tiles of conj(Vraw_i[b]) w[b], i = 0..k.
+// Products and warp sums in FP32 (the data are FP32); sums across tiles, warps
+// and CTAs in FP64 (GB300's FP64 rate is far below its FP32 rate, so FP64
+// stays out of per-element work).
+template <int W>
+__global__ void __launch_bounds__(kDotThreads) dots_kernel(const float2* __restrict__ V,
+                                                           const float2* __restrict__ w, int k, int B,
+                                                           long long N, int G, double2* partial,
+                                                           const int* active,
+                                                           unsigned long long* prof,
+                                                           unsigned long long prof_bytes) {
+  constexpr int NW = kDotThreads / 32;
+  constexpr int TILE = kDotThreads * kDotPacks * W;
+  const int b = blockIdx.y, cta = blockIdx.x;
   if (!active[b]) return;
-  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
-  __shared__ double2 red[kThreads / 32][129];
-  const long long base = (long long)chunk * kChunk;
-  float2 wv[kPer];
-  long long idxs[kPer];
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    const long long idx = base + e * kThreads + threadIdx.x;
-    const bool in = idx < N;
-    idxs[e] = in ? idx : 0;                      // loads stay in bounds; the product is zeroed
-    wv[e] = in ? w[(long long)b * N + idx] : make_float2(0.f, 0.f);
-  }
+  if (prof != nullptr && cta == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
+  __shared__ double2 red[NW][129];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 <= k; i0 += kDotBlock) {
-    float2 acc[kDotBlock];
+  for (int i = lane; i <= k; i += 32) red[warp][i] = make_double2(0.0, 0.0);
+  __syncwarp();
+  const long long ntile = (N + TILE - 1) / TILE;
+  const float2* wb = w + (long long)b * N;
+  for (long long t = cta; t < ntile; t += G) {
+    Pack<W> wv[kDotPacks];
+    long long off[kDotPacks];
 #pragma unroll
-    for (int u = 0; u < kDotBlock; ++u) {
-      const int i = min(i0 + u, k);              // repeats vector k past the end; not stored
-      const float2* vi = V + ((long long)i * B + b) * N;
-      float ax = 0.f, ay = 0.f;
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) {
-        const float2 v = vi[idxs[e]];
-        ax = fmaf(v.x, wv[e].x, fmaf(v.y, wv[e].y, ax));
-        ay = fmaf(v.x, wv[e].y, fmaf(-v.y, wv[e].x, ay));
-      }
-      acc[u] = make_float2(ax, ay);
+    for (int e = 0; e < kDotPacks; ++e) {
+      const long long j = t * TILE + (long long)(e * kDotThreads + threadIdx.x) * W;
+      const bool in = j < N;                     // N % W == 0: a pack is all in or all out
+      off[e] = in ? j : 0;                       // loads stay in bounds; the product is zeroed
+      wv[e] = in ? ldp<W>(wb + j) : zpack<W>();
     }
+    for (int i0 = 0; i0 <= k; i0 += kDotBlock) {
+      float2 acc[kDotBlock];
 #pragma unroll
-    for (int u = 0; u < kDotBlock; ++u) {
-      const float2 t = wsum32(acc[u]);
-      if (lane == 0 && i0 + u <= k) red[warp][i0 + u] = make_double2((double)t.x, (double)t.y);
+      for (int u = 0; u < kDotBlock; ++u) {
+        const int i = min(i0 + u, k);            // repeats vector k past the end; not stored
+        const float2* vi = V + ((long long)i * B + b) * N;
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int e = 0; e < kDotPacks; ++e) {
+          const Pack<W> v = ldp<W>(vi + off[e]);
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            ax = fmaf(v.c[q].x, wv[e].c[q].x, fmaf(v.c[q].y, wv[e].c[q].y, ax));
+            ay = fmaf(v.c[q].x, wv[e].c[q].y, fmaf(-v.c[q].y, wv[e].c[q].x, ay));
+          }
+        }
+        acc[u] = make_float2(ax, ay);
+      }
+#pragma unroll
+      for (int u = 0; u < kDotBlock; ++u) {
+        const float2 s = wsum32(acc[u]);
+        if (lane == 0 && i0 + u <= k) red[warp][i0 + u] = red[warp][i0 + u] + make_double2(s.x, s.y);
+      }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i <= k; i += kThreads) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int q = 0; q < kThreads / 32; ++q) s = s + red[q][i];
-    partial[((long long)b * 129 + i) * nchunk + chunk] = s;
+  for (int i = threadIdx.x; i <= k; i += kDotThreads) {
+    double2 s = red[0][i];
+    for (int q = 1; q < NW; ++q) s = s + red[q][i];
+    partial[((long long)b * 129 + i) * G + cta] = s;
   }
 }
 
-// w[b] -= sum_i coef[b][i] V_i[b]; optionally partial norms of the result
-__global__ void __launch_bounds__(kThreads) update_kernel(const float2* __restrict__ V, float2* w,
-                                                          const double2* coef, int k, int B,
-                                                          long long N, int nchunk, double* nrm_partial,
-                                                          const int* active, unsigned long long* prof,
-                                                          unsigned long long prof_bytes) {
-  const int b = blockIdx.y, chunk = blockIdx.x;
+// coef[b][i] = h_{i,k} = sig[b][i] sum_cta partial; H[b][k][i] (+)= coef.
+// One CTA of kReduceThreads per (i, b).
+constexpr int kReduceThreads = 128;
+__global__ void __launch_bounds__(kReduceThreads) reduce_dots_kernel(const double2* partial, int k,
+                                                                     int G, const double* sig,
+                                                                     double2* coef, double2* H,
+                                                                     int m, int accumulate,
+                                                                     const int* active) {
+  const int b = blockIdx.y, i = blockIdx.x;
   if (!active[b]) return;
-  if (prof != nullptr && chunk == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
-  __shared__ float2 c[129];
-  __shared__ double red[kThreads / 32];
-  for (int i = threadIdx.x; i <= k; i += kThreads) {
-    const double2 v = coef[(long long)b * 129 + i];
-    c[i] = make_float2((float)v.x, (float)v.y);
-  }
-  __syncthreads();
-  const long long base = (long long)chunk * kChunk;
-  float nrm32 = 0.f;
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    const long long idx = base + e * kThreads + threadIdx.x;
-    if (idx < N) {
-      float2 acc = w[(long long)b * N + idx];
-      for (int i = 0; i <= k; ++i) {
-        const float2 v = V[((long long)i * B + b) * N + idx];
-        acc.x -= c[i].x * v.x - c[i].y * v.y;
-        acc.y -= c[i].x * v.y + c[i].y * v.x;
-      }
-      w[(long long)b * N + idx] = acc;
-      nrm32 = fmaf(acc.x, acc.x, fmaf(acc.y, acc.y, nrm32));
-    }
-  }
-  if (nrm_partial) {
-    double nrm = (double)nrm32;
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int q = 0; q < kThreads / 32; ++q) s += red[q];
-      nrm_partial[(long long)b * nchunk + chunk] = s;
-    }
-  }
-}
-
-// coef[b][i] = sum_chunk partial; H[b][k][i] += coef (column k of the Hessenberg matrix)
-__global__ void reduce_dots_kernel(const double2* partial, int k, int nchunk, double2* coef,
-                                   double2* H, int m, int accumulate, const int* active) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i > k) return;
+  __shared__ double2 red[kReduceThreads / 32];
+  const double2* p = partial + ((long long)b * 129 + i) * G;
   double2 s = make_double2(0.0, 0.0);
-  for (int c = lane; c < nchunk; c += 32) s = s + partial[((long long)b * 129 + i) * nchunk + c];
+  for (int c = threadIdx.x; c < G; c += kReduceThreads) s = s + p[c];
   s = wsum(s);
-  if (lane == 0) {
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = red[0];
+    for (int q = 1; q < kReduceThreads / 32; ++q) s = s + red[q];
+    s = sig[(long long)b * (m + 1) + i] * s;
     coef[(long long)b * 129 + i] = s;
     double2* h = H + ((long long)b * m + k) * (m + 1) + i;
     *h = accumulate ? (*h + s) : s;
   }
+}
+
+enum { UPD_FINAL = 0, UPD_DGKS = 1 };
+
+// w[b] -= sum_i coef[b][i] sig[b][i] Vraw_i[b], then ||w[b]||.  The last CTA
+// of right-hand side b to finish (an atomic ticket) sums the norm partials:
+//   UPD_FINAL: nrm[b] = h_{k+1,k} = ||w||, sig[b][k+1] = 1 / h_{k+1,k};
+//   UPD_DGKS:  the DGKS test (re-orthogonalise only where the projection
+//              removed most of w, ||w'||^2 < (1/2)(||w'||^2 + ||h||^2)), and
+//              the UPD_FINAL results where no second pass is needed.
+template <int W>
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(const float2* __restrict__ V, float2* w,
+                                                             const double2* coef, double* sig,
+                                                             int k, int m, int B, long long N, int G,
+                                                             double* nrm_partial, int* ticket,
+                                                             int mode, double* nrm_out, int* again,
+                                                             const int* mask,
+                                                             unsigned long long* prof,
+                                                             unsigned long long prof_bytes) {
+  const int b = blockIdx.y, cta = blockIdx.x;
+  if (!mask[b]) return;
+  if (prof != nullptr && cta == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
+  __shared__ float2 c[129];
+  __shared__ double red[kUpdThreads / 32];
+  __shared__ int last;
+  for (int i = threadIdx.x; i <= k; i += kUpdThreads) {
+    const double2 v = sig[(long long)b * (m + 1) + i] * coef[(long long)b * 129 + i];
+    c[i] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const long long j = ((long long)cta * kUpdThreads + threadIdx.x) * W;
+  const bool in = j < N;
+  const long long off = in ? j : 0;
+  float2* wb = w + (long long)b * N;
+  Pack<W> acc = in ? ldp<W>(wb + j) : zpack<W>();
+  // basis vectors from k down to 0: the dots kernel just read them from 0 up
+  // to k, so the most recent ones are still in L2
+  int i = k;
+  for (; i + 1 >= kUpdBlock; i -= kUpdBlock) {
+    Pack<W> v[kUpdBlock];
+#pragma unroll
+    for (int u = 0; u < kUpdBlock; ++u) v[u] = ldp<W>(V + ((long long)(i - u) * B + b) * N + off);
+#pragma unroll
+    for (int u = 0; u < kUpdBlock; ++u) {
+      const float2 ci = c[i - u];
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        acc.c[q].x -= ci.x * v[u].c[q].x - ci.y * v[u].c[q].y;
+        acc.c[q].y -= ci.x * v[u].c[q].y + ci.y * v[u].c[q].x;
+      }
+    }
+  }
+  for (; i >= 0; --i) {
+    const float2 ci = c[i];
+    const Pack<W> v = ldp<W>(V + ((long long)i * B + b) * N + off);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      acc.c[q].x -= ci.x * v.c[q].x - ci.y * v.c[q].y;
+      acc.c[q].y -= ci.x * v.c[q].y + ci.y * v.c[q].x;
+    }
+  }
+  float nrm32 = 0.f;
+  if (in) {
+    stp<W>(wb + j, acc);
+#pragma unroll
+    for (int q = 0; q < W; ++q) nrm32 = fmaf(acc.c[q].x, acc.c[q].x, fmaf(acc.c[q].y, acc.c[q].y, nrm32));
+  }
+  double nrm = (double)nrm32;
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kUpdThreads / 32; ++q) s += red[q];
+    nrm_partial[(long long)b * G + cta] = s;
+    __threadfence();
+    last = (atomicAdd(&ticket[b], 1) == G - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  // last CTA of right-hand side b: every other CTA's partial is visible
+  __threadfence();
+  double s = 0.0;
+  for (int q = threadIdx.x; q < G; q += kUpdThreads) s += __ldcg(nrm_partial + (long long)b * G + q);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __syncthreads();                               // red[] reuse
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double w2 = 0.0;
+  for (int q = 0; q < kUpdThreads / 32; ++q) w2 += red[q];
+  bool fin = true;
+  if (mode == UPD_DGKS) {
+    double hh = 0.0;
+    for (int q = lane; q <= k; q += 32) hh += abs2(coef[(long long)b * 129 + q]);
+    for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    const bool redo = w2 < 0.5 * (w2 + hh);
+    if (lane == 0) again[b] = redo ? 1 : 0;
+    fin = !redo;
+  }
+  if (lane == 0) {
+    ticket[b] = 0;                               // ready for the next launch
+    if (fin) {
+      const double h = sqrt(w2);
+      nrm_out[b] = h;
+      sig[(long long)b * (m + 1) + k + 1] = h > 1e-300 ? 1.0 / h : 0.0;
+    }
+  }
+}
+
+// One Givens step per right-hand side (one warp each): finish column k
+// (h_{k+1,k} = nrm), apply the k earlier rotations, form the new one, update
+// g and test convergence.  The column and the rotations are staged in shared
+// memory so the sequential rotation chain does not wait on global memory.  It
+// runs beside the next matvec (which needs only sig[b][k+1]); its FP64 chain,
+// a few microseconds on a part with GB300's FP64 latency, is then off the
+// critical path.
+__global__ void __launch_bounds__(128) givens_kernel(double2* H, double2* cs, double2* sn, double2* g,
+                                                     const double* nrm, int k, int m, int B,
+                                                     int* active, int* again, int* iters,
+                                                     const double* tol_abs, int* count) {
+  __shared__ double2 sh[4][130], sc[4][128], ss[4][128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * 4 + warp;
+  if (b >= B || !active[b]) return;            // warp-uniform; no block barrier below
+  double2* h = H + ((long long)b * m + k) * (m + 1);
+  double2* c = cs + (long long)b * m;
+  double2* s = sn + (long long)b * m;
+  for (int i = lane; i <= k; i += 32) sh[warp][i] = h[i];
+  for (int i = lane; i < k; i += 32) {
+    sc[warp][i] = c[i];
+    ss[warp][i] = s[i];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    count[b] += 1;
+    double2* hh = sh[warp];
+    const double hk1 = nrm[b];
+    hh[k + 1] = make_double2(hk1, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double2 ci = sc[warp][i], si = ss[warp][i];
+      const double2 t = ci * hh[i] + si * hh[i + 1];
+      hh[i + 1] = (-1.0) * (conjg(si) * hh[i]) + conjg(ci) * hh[i + 1];
+      hh[i] = t;
+    }
+    const double2 x = hh[k], y = hh[k + 1];
+    const double den = sqrt(abs2(x) + abs2(y));
+    double2 ck, sk;
+    if (den == 0.0) {
+      ck = make_double2(1.0, 0.0);
+      sk = make_double2(0.0, 0.0);
+    } else {
+      ck = (1.0 / den) * conjg(x);
+      sk = (1.0 / den) * conjg(y);
+    }
+    c[k] = ck;
+    s[k] = sk;
+    hh[k] = ck * x + sk * y;
+    hh[k + 1] = make_double2(0.0, 0.0);
+    double2* gb = g + (long long)b * (m + 1);
+    const double2 gk = gb[k];
+    gb[k + 1] = (-1.0) * (conjg(sk) * gk);
+    gb[k] = ck * gk;
+    iters[b] = k + 1;
+    const double res2 = abs2(gb[k + 1]);
+    const double tol = tol_abs[b];
+    const bool breakdown = !(hk1 > 1e-300) || !(abs2(hh[k]) > 0.0);
+    if (res2 <= tol * tol || breakdown || k + 1 == m || !(res2 == res2)) {
+      active[b] = 0;
+      again[b] = 0;
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i <= k + 1; i += 32) h[i] = sh[warp][i];
 }
 
 // out[b] = sqrt(sum_chunk partial[b][chunk])
@@ -195,99 +390,6 @@ __global__ void __launch_bounds__(kThreads) norm32_kernel(const float2* v, long 
   }
 }
 
-// One Givens step per RHS (one warp each): finish column k (h_{k+1,k} = nrm),
-// apply the k earlier rotations, form the new one, update g, test convergence
-// and store 1/h_{k+1,k} for the normalisation of the next basis vector.  The
-// column and the rotations are staged in shared memory so the sequential
-// rotation chain does not wait on global memory.
-__global__ void __launch_bounds__(128) givens_kernel(double2* H, double2* cs, double2* sn, double2* g,
-                                                     const double* nrm, double* inv, int k, int m,
-                                                     int B, int* active, int* iters,
-                                                     const double* tol_abs, int* count) {
-  __shared__ double2 sh[4][130], sc[4][128], ss[4][128];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * 4 + warp;
-  if (b >= B || !active[b]) return;            // warp-uniform; no block barrier below
-  double2* h = H + ((long long)b * m + k) * (m + 1);
-  double2* c = cs + (long long)b * m;
-  double2* s = sn + (long long)b * m;
-  for (int i = lane; i <= k; i += 32) sh[warp][i] = h[i];
-  for (int i = lane; i < k; i += 32) {
-    sc[warp][i] = c[i];
-    ss[warp][i] = s[i];
-  }
-  __syncwarp();
-  if (lane == 0) {
-    count[b] += 1;
-    double2* hh = sh[warp];
-    const double hk1 = nrm[b];
-    hh[k + 1] = make_double2(hk1, 0.0);
-    for (int i = 0; i < k; ++i) {
-      const double2 ci = sc[warp][i], si = ss[warp][i];
-      const double2 t = ci * hh[i] + si * hh[i + 1];
-      hh[i + 1] = (-1.0) * (conjg(si) * hh[i]) + conjg(ci) * hh[i + 1];
-      hh[i] = t;
-    }
-    const double2 a = hh[k], bb = hh[k + 1];
-    const double den = sqrt(abs2(a) + abs2(bb));
-    double2 ck, sk;
-    if (den == 0.0) {
-      ck = make_double2(1.0, 0.0);
-      sk = make_double2(0.0, 0.0);
-    } else {
-      ck = (1.0 / den) * conjg(a);
-      sk = (1.0 / den) * conjg(bb);
-    }
-    c[k] = ck;
-    s[k] = sk;
-    hh[k] = ck * a + sk * bb;
-    hh[k + 1] = make_double2(0.0, 0.0);
-    double2* gb = g + (long long)b * (m + 1);
-    const double2 gk = gb[k];
-    gb[k + 1] = (-1.0) * (conjg(sk) * gk);
-    gb[k] = ck * gk;
-    iters[b] = k + 1;
-    const double res = sqrt(abs2(gb[k + 1]));
-    const bool breakdown = !(hk1 > 1e-300) || !(sqrt(abs2(hh[k])) > 0.0);
-    if (res <= tol_abs[b] || breakdown || k + 1 == m || !(res == res)) active[b] = 0;
-    inv[b] = hk1 > 1e-300 ? 1.0 / hk1 : 0.0;
-  }
-  __syncwarp();
-  for (int i = lane; i <= k + 1; i += 32) h[i] = sh[warp][i];
-}
-
-// DGKS test after the first Gram-Schmidt pass: re-orthogonalise only when the
-// projection removed most of w, ||w'||^2 < (1/2) (||w'||^2 + ||h||^2).
-__global__ void dgks_kernel(const double2* coef, const double* nrm, int k, int B, const int* active,
-                            int* again) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  int r = 0;
-  if (active[b]) {
-    double hh = 0.0;
-    for (int i = 0; i <= k; ++i) hh += abs2(coef[(long long)b * 129 + i]);
-    const double w2 = nrm[b] * nrm[b];
-    r = (w2 < 0.5 * (w2 + hh)) ? 1 : 0;
-  }
-  again[b] = r;
-}
-
-// V_{k+1}[b] = w[b] * inv[b]  (only for RHS still active after the Givens step)
-__global__ void __launch_bounds__(kThreads) scale_into_kernel(const float2* w, float2* dst,
-                                                              const double* inv, long long N,
-                                                              const int* active) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const float s = (float)inv[b];
-  for (int e = 0; e < kPer; ++e) {
-    const long long idx = (long long)blockIdx.x * kChunk + e * kThreads + threadIdx.x;
-    if (idx < N) {
-      const float2 v = w[(long long)b * N + idx];
-      dst[(long long)b * N + idx] = make_float2(s * v.x, s * v.y);
-    }
-  }
-}
-
 // y = R^-1 g over the iters[b] columns of the rotated Hessenberg matrix
 __global__ void backsolve_kernel(const double2* H, const double2* g, double2* y, int m, int B,
                                  const int* iters) {
@@ -305,15 +407,16 @@ __global__ void backsolve_kernel(const double2* H, const double2* g, double2* y,
   }
 }
 
-// d[b] += sum_{j < iters[b]} y[b][j] V_j[b]
+// d[b] += sum_{j < iters[b]} y[b][j] V_j[b]  (V_j = sig[b][j] Vraw_j)
 __global__ void __launch_bounds__(kThreads) combine_kernel(const float2* V, float2* d, const double2* y,
-                                                           int B, long long N, const int* iters) {
+                                                           const double* sig, int m, int B,
+                                                           long long N, const int* iters) {
   const int b = blockIdx.y;
   const int kk = iters[b];
   if (kk == 0) return;
   __shared__ float2 c[129];
   for (int i = threadIdx.x; i < kk; i += kThreads) {
-    const double2 v = y[(long long)b * 129 + i];
+    const double2 v = sig[(long long)b * (m + 1) + i] * y[(long long)b * 129 + i];
     c[i] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
@@ -359,20 +462,22 @@ __global__ void __launch_bounds__(kThreads) residual32_kernel(const float2* rhs,
   }
 }
 
-// start of a cycle: beta = ||r||, g = (beta, 0, ...), iters = 0, active = want && beta > tol
-__global__ void cycle_start_kernel(const double* beta, double2* g, double* inv, int m, int B,
-                                   const int* want, int* active, int* iters, const double* tol_abs,
-                                   int* count) {
+// start of a cycle: beta = ||r||, g = (beta, 0, ...), iters = 0, active = want && beta > tol,
+// and basis vector 0 = r / beta (slot 0 holds r, its factor is 1 / beta)
+__global__ void cycle_start_kernel(const double* beta, double2* g, double* sig, int m, int B,
+                                   const int* want, int* active, int* again, int* iters,
+                                   const double* tol_abs, int* count) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   iters[b] = 0;
   if (count && want[b]) count[b] += 1;   // the residual matvec that produced beta
   const bool go = want[b] && beta[b] > tol_abs[b] && beta[b] == beta[b];
   active[b] = go ? 1 : 0;
+  again[b] = 0;
   double2* gb = g + (long long)b * (m + 1);
   for (int i = 0; i <= m; ++i) gb[i] = make_double2(0.0, 0.0);
   gb[0] = make_double2(go ? beta[b] : 0.0, 0.0);
-  inv[b] = go ? 1.0 / beta[b] : 0.0;
+  sig[(long long)b * (m + 1)] = go ? 1.0 / beta[b] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -505,12 +610,14 @@ struct SolverState {
   int B = 0, m = 0, path = -1;
   long long N = 0;
   int nchunk = 0;
+  int G = 0, Gu = 0;                // CTAs per RHS of the dots and update kernels
+  int wide = 0;                     // 16-byte loads in dots / update (N even)
   size_t bytes = 0;
   char* base = nullptr;
   float2 *V, *W, *d, *r32;
   double2 *H, *cs, *sn, *g, *coef, *partial;
-  double *nrm_partial, *nrm, *inv, *beta, *tol_abs, *rnorm, *bnorm, *pb;
-  int *active, *iters, *want, *count_it, *count_mv, *again;
+  double *nrm_partial, *nrm, *sig, *beta, *tol_abs, *rnorm, *bnorm, *pb;
+  int *active, *iters, *want, *count_it, *count_mv, *again, *ticket;
   double2 *x, *b64, *r64, *ax64;
   float2* chi32;
   double2* chi64;
@@ -519,6 +626,10 @@ struct SolverState {
   // default stream), ordered after and before the caller's stream by events
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // the Givens step runs on a side stream beside the next matvec
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool givens_pending = false;
   cudaGraphExec_t exec = nullptr;
   const void* graph_chi = nullptr;
   const void* graph_ws = nullptr;
@@ -544,8 +655,14 @@ static void release_state(SolverState* st) {
     cudaStreamSynchronize(st->stream);
     cudaStreamDestroy(st->stream);
   }
+  if (st->aux) {
+    cudaStreamSynchronize(st->aux);
+    cudaStreamDestroy(st->aux);
+  }
   if (st->ev_in) cudaEventDestroy(st->ev_in);
   if (st->ev_out) cudaEventDestroy(st->ev_out);
+  if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+  if (st->ev_join) cudaEventDestroy(st->ev_join);
   cudaFree(st->base);
   delete st;
 }
@@ -561,7 +678,7 @@ template <typename T> static T* carve(char*& p, size_t count) {
   return r;
 }
 
-static size_t carve_bytes(int B, int m, long long N, int nchunk) {
+static size_t carve_bytes(int B, int m, long long N, int nchunk, int G, int Gu) {
   char* p = nullptr;
   carve<float2>(p, (size_t)(m + 1) * B * N);          // V
   carve<float2>(p, (size_t)B * N);                    // W
@@ -572,11 +689,12 @@ static size_t carve_bytes(int B, int m, long long N, int nchunk) {
   carve<double2>(p, (size_t)B * m);                   // sn
   carve<double2>(p, (size_t)B * (m + 1));             // g
   carve<double2>(p, (size_t)B * 129);                 // coef / y
-  carve<double2>(p, (size_t)B * 129 * nchunk);        // partial dots
-  carve<double>(p, (size_t)B * nchunk);               // norm partials
-  for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm inv beta tol_abs rnorm bnorm
+  carve<double2>(p, (size_t)B * 129 * G);             // partial dots
+  carve<double>(p, (size_t)B * std::max(nchunk, Gu)); // norm partials
+  for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm beta tol_abs rnorm bnorm
+  carve<double>(p, (size_t)B * (m + 1));              // sig
   carve<double>(p, (size_t)B * nchunk);               // pb
-  for (int i = 0; i < 6; ++i) carve<int>(p, B);       // active iters want counters again
+  for (int i = 0; i < 7; ++i) carve<int>(p, B);       // active iters want counters again ticket
   for (int i = 0; i < 4; ++i) carve<double2>(p, (size_t)B * N);   // x b64 r64 ax64
   carve<float2>(p, (size_t)N / 3);                    // chi32
   carve<double2>(p, (size_t)N / 3);                   // chi64
@@ -590,6 +708,11 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
     *out = st;
     return VIE_OK;
   }
+  const int wide = (N % 2 == 0) ? 1 : 0;
+  const int W = wide ? 2 : 1;
+  const long long dtile = (long long)kDotThreads * kDotPacks * W;
+  const int G = (int)std::min<long long>((N + dtile - 1) / dtile, kMaxDotCtas);
+  const int Gu = (int)((N + (long long)kUpdThreads * W - 1) / ((long long)kUpdThreads * W));
   release_state(st);
   op->solver = nullptr;
   op->solve_ws.bytes = 0;
@@ -598,17 +721,23 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->m = m;
   st->N = N;
   st->nchunk = (int)((N + kChunk - 1) / kChunk);
-  st->bytes = carve_bytes(B, m, N, st->nchunk);
+  st->G = G;
+  st->Gu = Gu;
+  st->wide = wide;
+  st->bytes = carve_bytes(B, m, N, st->nchunk, st->G, st->Gu);
   cudaError_t e = cudaMalloc(&st->base, st->bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete st;
-    set_error("solver workspace of %zu bytes could not be allocated", (size_t)carve_bytes(B, m, N, (int)((N + kChunk - 1) / kChunk)));
+    set_error("solver workspace of %zu bytes could not be allocated", st->bytes);
     return VIE_ERR_OOM;
   }
   if ((e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&st->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
     release_state(st);
     return cuda_status(e, "solver stream");
   }
@@ -623,15 +752,16 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->sn = carve<double2>(p, (size_t)B * m);
   st->g = carve<double2>(p, (size_t)B * (m + 1));
   st->coef = carve<double2>(p, (size_t)B * 129);
-  st->partial = carve<double2>(p, (size_t)B * 129 * nc);
-  st->nrm_partial = carve<double>(p, (size_t)B * nc);
+  st->partial = carve<double2>(p, (size_t)B * 129 * st->G);
+  st->nrm_partial = carve<double>(p, (size_t)B * std::max(nc, st->Gu));
   st->nrm = carve<double>(p, B);
-  st->inv = carve<double>(p, B);
+  carve<double>(p, B);
   st->beta = carve<double>(p, B);
   st->tol_abs = carve<double>(p, B);
   st->rnorm = carve<double>(p, B);
   st->bnorm = carve<double>(p, B);
   carve<double>(p, B);
+  st->sig = carve<double>(p, (size_t)B * (m + 1));
   st->pb = carve<double>(p, (size_t)B * nc);
   st->active = carve<int>(p, B);
   st->iters = carve<int>(p, B);
@@ -639,66 +769,94 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->count_it = carve<int>(p, B);
   st->count_mv = carve<int>(p, B);
   st->again = carve<int>(p, B);
+  st->ticket = carve<int>(p, B);
   st->x = carve<double2>(p, (size_t)B * N);
   st->b64 = carve<double2>(p, (size_t)B * N);
   st->r64 = carve<double2>(p, (size_t)B * N);
   st->ax64 = carve<double2>(p, (size_t)B * N);
   st->chi32 = carve<float2>(p, (size_t)N / 3);
   st->chi64 = carve<double2>(p, (size_t)N / 3);
+  // tickets start at zero; each use returns its counter to zero
+  if ((e = cudaMemset(st->ticket, 0, B * sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(st->again, 0, B * sizeof(int))) != cudaSuccess) {
+    release_state(st);
+    return cuda_status(e, "solver workspace");
+  }
   op->solver = st;
   op->solve_ws.bytes = st->bytes;
   *out = st;
   return VIE_OK;
 }
 
-// One Arnoldi step k (CGS2) for all active RHS.
+// Wait on stream s for the Givens step running on the side stream.
+static int join_givens(SolverState* st, cudaStream_t s) {
+  if (!st->givens_pending) return VIE_OK;
+  VIE_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
+  st->givens_pending = false;
+  return VIE_OK;
+}
+
+// One Arnoldi step k for all active RHS: w = A V_k into basis slot k+1, one
+// or two classical Gram-Schmidt passes (the second where the DGKS test asks
+// for it), then the Givens step on the side stream, joined before the next
+// step's Gram-Schmidt (the next matvec needs only sig[b][k+1]; a right-hand
+// side that the Givens step retires meanwhile is skipped from then on and
+// its extra matvec output is never read).
 static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, int k, int path,
                         int adjoint, int passes, cudaStream_t s) {
-  const int B = st->B, m = st->m, nc = st->nchunk;
+  const int B = st->B, m = st->m, G = st->G, Gu = st->Gu;
   const long long N = st->N;
   const float2* vk = st->V + (long long)k * B * N;
-  float2* w = st->W;
-  // w = A v_k
+  float2* w = st->V + (long long)(k + 1) * B * N;
+  // w = A (sig_k Vraw_k)
   if (!adjoint)
-    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s));
+    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s,
+                               st->sig + k, m + 1));
   else
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi, vk,
-                               st->active, s));
-  dim3 grid(nc, B);
-  const int rblocks = (k + 1 + 7) / 8;
+                               st->active, s, st->sig + k, m + 1));
+  VIE_TRY(join_givens(st, s));
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
-  // classical Gram-Schmidt; a second pass only where the DGKS test asks for it
   for (int pass = 0; pass < passes; ++pass) {
     const int* mask = pass == 0 ? st->active : st->again;
+    const int mode = (pass == 0 && passes > 1) ? UPD_DGKS : UPD_FINAL;
     {
       ProfScope ps(PF_DOTS, s);
-      dots_kernel<<<grid, kThreads, 0, s>>>(st->V, w, k, B, N, nc, st->partial, mask,
-                                            prof_bytes(PF_DOTS), (k + 2) * vec);
+      if (st->wide)
+        dots_kernel<2><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, st->partial, mask,
+                                                          prof_bytes(PF_DOTS), (k + 2) * vec);
+      else
+        dots_kernel<1><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, st->partial, mask,
+                                                          prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
-      reduce_dots_kernel<<<dim3(rblocks, B), 256, 0, s>>>(st->partial, k, nc, st->coef, st->H, m,
-                                                          pass, mask);
+      reduce_dots_kernel<<<dim3(k + 1, B), kReduceThreads, 0, s>>>(st->partial, k, G, st->sig,
+                                                                   st->coef, st->H, m, pass, mask);
     }
     {
       ProfScope ps(PF_UPDATE, s);
-      update_kernel<<<grid, kThreads, 0, s>>>(st->V, w, st->coef, k, B, N, nc, st->nrm_partial, mask,
-                                              prof_bytes(PF_UPDATE), (k + 3) * vec);
-    }
-    {
-      ProfScope ps(PF_SMALL, s);
-      reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->nrm, mask);
-      if (pass == 0 && passes > 1)
-        dgks_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->coef, st->nrm, k, B, st->active, st->again);
+      if (st->wide)
+        update_kernel<2><<<dim3(Gu, B), kUpdThreads, 0, s>>>(
+            st->V, w, st->coef, st->sig, k, m, B, N, Gu, st->nrm_partial, st->ticket, mode, st->nrm,
+            st->again, mask, prof_bytes(PF_UPDATE), (k + 3) * vec);
+      else
+        update_kernel<1><<<dim3(Gu, B), kUpdThreads, 0, s>>>(
+            st->V, w, st->coef, st->sig, k, m, B, N, Gu, st->nrm_partial, st->ticket, mode, st->nrm,
+            st->again, mask, prof_bytes(PF_UPDATE), (k + 3) * vec);
     }
   }
+  // the Givens step beside the next matvec
+  VIE_CUDA(cudaEventRecord(st->ev_fork, s));
+  VIE_CUDA(cudaStreamWaitEvent(st->aux, st->ev_fork, 0));
   {
-    ProfScope ps(PF_SMALL, s);
-    givens_kernel<<<(B + 3) / 4, 128, 0, s>>>(st->H, st->cs, st->sn, st->g, st->nrm, st->inv, k, m,
-                                              B, st->active, st->iters, st->tol_abs, st->count_it);
-    scale_into_kernel<<<grid, kThreads, 0, s>>>(w, st->V + (long long)(k + 1) * B * N, st->inv, N,
-                                                st->active);
+    ProfScope ps(PF_SMALL, st->aux);
+    givens_kernel<<<(B + 3) / 4, 128, 0, st->aux>>>(st->H, st->cs, st->sn, st->g, st->nrm, k, m, B,
+                                                    st->active, st->again, st->iters, st->tol_abs,
+                                                    st->count_it);
   }
+  VIE_CUDA(cudaEventRecord(st->ev_join, st->aux));
+  st->givens_pending = true;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "arnoldi");
   return VIE_OK;
@@ -710,10 +868,11 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
   const int B = st->B, m = st->m, nc = st->nchunk;
   const long long N = st->N;
   dim3 grid(nc, B);
+  VIE_TRY(join_givens(st, s));
   {
     ProfScope ps(PF_SMALL, s);
     backsolve_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
-    combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, B, N, st->iters);
+    combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, st->sig, m, B, N, st->iters);
   }
   // W = A d for the RHS still wanted
   if (!adjoint)
@@ -726,9 +885,9 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
     residual32_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->W, st->V, N, nc, st->nrm_partial,
                                                 st->want);
     reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
-    cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, m, B, st->want,
-                                                   st->active, st->iters, st->tol_abs, st->count_mv);
-    scale_into_kernel<<<grid, kThreads, 0, s>>>(st->V, st->V, st->inv, N, st->active);
+    cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->sig, m, B, st->want,
+                                                   st->active, st->again, st->iters, st->tol_abs,
+                                                   st->count_mv);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "cycle tail");
@@ -737,6 +896,7 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
 
 static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int path, int adjoint,
                      int passes, bool use_graph, cudaStream_t s) {
+  st->givens_pending = false;                 // every cycle ends joined
   if (!use_graph) {
     for (int k = 0; k < st->m; ++k) VIE_TRY(arnoldi_step(op, st, chi, k, path, adjoint, passes, s));
     return cycle_tail(op, st, chi, path, adjoint, s);
@@ -800,9 +960,11 @@ static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint,
   // first cycle: d = 0, so the residual is r32 itself
   norm32_kernel<<<grid, kThreads, 0, s>>>(st->r32, N, nc, st->nrm_partial, st->want);
   reduce_norm_kernel<<<B, 32, 0, s>>>(st->nrm_partial, nc, st->beta, st->want);
-  cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->inv, st->m, B, st->want,
-                                                 st->active, st->iters, st->tol_abs, nullptr);
-  scale_into_kernel<<<grid, kThreads, 0, s>>>(st->r32, st->V, st->inv, N, st->active);
+  cycle_start_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->beta, st->g, st->sig, st->m, B, st->want,
+                                                 st->active, st->again, st->iters, st->tol_abs,
+                                                 nullptr);
+  // basis slot 0 = r32, with factor 1 / beta
+  VIE_CUDA(cudaMemcpyAsync(st->V, st->r32, (size_t)B * N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   VIE_CUDA(cudaGetLastError());
   std::vector<int> act(B);
   for (int cycle = 0; cycle < max_outer; ++cycle) {

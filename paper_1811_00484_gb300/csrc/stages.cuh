@@ -97,11 +97,15 @@ __device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0,
   const int ncols = min(TW, a.ncol - c0);
 
   for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                       ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                       : 1.f;
   const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
   for (int e = tid; e < a.lin * TW; e += nth) {
     const int c = e % TW, p = e / TW;
     if (c < ncols) {
       C v = in[p * a.in_ls + c];
+      if (a.flags & PRO_RSCALE) v = rs * v;
       if (a.flags & PRO_CONJ) v = conjg(v);
       if (a.flags & PRO_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
       tile[tile_slot(p, c)] = v;
@@ -149,7 +153,8 @@ __device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0,
     const long long oi = p * a.out_ls + c;
     if (a.flags & (EPI_SUB | EPI_ADD)) {
       if (a.flags & EPI_CHI) v = a.chi[o * a.chi_os + p * a.chi_ls + (long long)(c0 + c)] * v;
-      const C w = a.addend[obase + oi];
+      C w = a.addend[obase + oi];
+      if (a.flags & EPI_RSCALE) w = rs * w;
       v = (a.flags & EPI_SUB) ? (w - v) : (w + v);
     }
     out[oi] = v;
@@ -161,7 +166,8 @@ __device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0,
 // fall in different banks (at most 2-way for the radices used, 4-way at R=10).
 __device__ __forceinline__ int ghalf_slot(int k) { return k + (k >> 3); }
 
-__host__ __device__ constexpr size_t fused_warp_smem(int R, int H3, int r3max) {
+__host__ __device__ constexpr size_t fused_warp_smem(int R, int H3, int r2max, int r3max) {
+  (void)r2max;
   return (size_t)(32 * R + 6 * ((H3 - 1) + ((H3 - 1) >> 3) + 1) + 6 * r3max) * sizeof(float2);
 }
 

@@ -67,7 +67,9 @@ enum {
   EPI_CONJ = 4,      // conjugate the (scaled) result
   EPI_SUB = 8,       // out = addend - (chi?) result
   EPI_ADD = 16,      // out = addend + result
-  EPI_CHI = 32       // multiply the result by chi before EPI_SUB
+  EPI_CHI = 32,      // multiply the result by chi before EPI_SUB
+  PRO_RSCALE = 64,   // multiply the input by the real per-RHS factor rscale[rhs * rscale_stride]
+  EPI_RSCALE = 128   // multiply the addend by that factor (EPI_SUB / EPI_ADD)
 };
 
 // ---------------------------------------------------------------------------
@@ -103,6 +105,8 @@ template <typename T> struct LineArgs {
   const cx<T>* roots;      // N-th roots of unity exp(-2 pi i m / N), m < N
   const cx<T>* chi;        // scalar field (PRO_CHI / EPI_CHI)
   const cx<T>* addend;     // EPI_SUB / EPI_ADD, laid out like `out`
+  const double* rscale;    // PRO_RSCALE / EPI_RSCALE: per-RHS real factor
+  long long rscale_stride;
   FftPlan plan;
   int lin, lout;           // points loaded (rest zero) / points stored
   int inverse;
@@ -151,7 +155,7 @@ struct vie_op {
   int flags;
   TuckerComp comp[6];
   int rmax[3];
-  // slab cores S_c[k1] = core_c x1 U1_c[k1, :], rebuilt at every matvec
+  // slab cores S_c[k1] = core_c x1 U1_c[k1, :] (mode 1 of eq. (13)), formed at setup
   float2* slab32 = nullptr;  double2* slab64 = nullptr;
   size_t slab_stride;        // elements per component: H1 * rmax2 * rmax3
   // stored spectra (optional)
@@ -202,7 +206,7 @@ double wavenumber(double freq_hz);
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
-                cudaStream_t s);
+                cudaStream_t s, const double* rscale = nullptr, long long rscale_stride = 0);
 int ensure_workspace(vie_op* op, int B);
 // The four line-stage launches of one matvec (x, y, inverse y, inverse x).
 template <typename T> struct LineStages {
@@ -211,13 +215,17 @@ template <typename T> struct LineStages {
 template <typename T>
 LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B,
                                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-                               const int* active);
+                               const int* active, const double* rscale = nullptr,
+                               long long rscale_stride = 0);
 // the same stages with an explicit scratch buffer of at least matvec_scratch_bytes() bytes
 template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-               const int* active, cudaStream_t s);
+               const int* active, cudaStream_t s, const double* rscale = nullptr,
+               long long rscale_stride = 0);
 size_t workspace_bytes_for(const vie_op* op, int B);
+
+template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
 
 // setup internals (setup.cu)
 int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,

@@ -89,6 +89,18 @@ def test_refined_solve_n16_against_oracle_gmres(use_graph):
     assert rel(wg, w_ref) <= 1e-7
 
 
+def test_odd_voxel_count_solve():
+    """All-odd grid: 3 n1 n2 n3 is odd, so the Gram-Schmidt kernels use 8-byte loads."""
+    wl, T, Ghat, Gt, op = case((5, 7, 9), tol_svd=1e-8, seed=4)
+    assert (3 * 5 * 7 * 9) % 2 == 1
+    w, info = op.solve(dev(wl.chi, C128), dev(wl.einc, C128), tol=1e-10)
+    assert info["converged"] and info["relres"] <= 1e-10, info
+    assert residual(Gt, wl.chi, wl.einc, host(w)) <= 2e-10
+    w32, info32 = op.solve(dev(wl.chi), dev(wl.einc), tol=1e-6, use_graph=False)
+    assert info32["converged"]
+    assert residual(Gt, wl.chi, wl.einc, host(w32)) <= 2e-6
+
+
 def test_graph_and_direct_launches_agree():
     wl, T, Ghat, Gt, op = case((8, 6, 10), tol_svd=1e-8, seed=3)
     w1, i1 = op.solve(dev(wl.chi), dev(wl.einc), tol=1e-9, use_graph=True)
