@@ -141,8 +141,14 @@ __global__ void __launch_bounds__(256, 3) fused_z_kernel(const FusedArgs<T> a) {
 
 // Register-resident variant for P3 = 32 R: one CTA of four warps per (k1, k2)
 // mirror group, see fused_warp_group.
+// Resident CTAs per SM the register budget is sized for (up to radix 4: 96
+// registers, five CTAs of four warps; radix 5-6: 128; radix 8: 168).
+__host__ __device__ constexpr int fused_min_blocks(int R) {
+  return R <= 4 ? 5 : (R <= 6 ? 4 : (R <= 8 ? 3 : 2));
+}
+
 template <int R, bool STORED>
-__global__ void __launch_bounds__(128) fused_warp_kernel(const FusedArgs<float> a) {
+__global__ void __launch_bounds__(128, fused_min_blocks(R)) fused_warp_kernel(const FusedArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fused_warp_group<R, STORED>(a, blockIdx.x, reinterpret_cast<float2*>(smem_raw));
 }

@@ -8,6 +8,8 @@
 // (points lin..N-1 read as zero), cropping (only points < lout stored),
 // conjugation, the contrast product and the final scale/subtract of the
 // system operator are fused into the load and store loops.
+#include <cstdint>
+
 #include "stages.cuh"
 
 namespace vie {
@@ -75,11 +77,54 @@ __global__ void __launch_bounds__(256, 3) line_fft_kernel(const LineArgs<T> a) {
 
 // Register-resident variant for N = 32 R (columns contiguous in memory): one
 // 16-column tile per CTA, see line_warp_tile.
+// Resident CTAs per SM the register budget is sized for: up to radix 4 the
+// kernel fits 40 registers without spills (six 256-thread CTAs per SM), up to
+// radix 8 64 registers; larger radices get more registers than that.
+__host__ __device__ constexpr int line_min_blocks(int R) { return R <= 4 ? 6 : (R <= 8 ? 4 : 2); }
+
 template <int R, bool HALF>
-__global__ void __launch_bounds__(256) line_warp_kernel(const LineArgs<float> a) {
+__global__ void __launch_bounds__(256, line_min_blocks(R)) line_warp_kernel(const LineArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   line_warp_tile<R, HALF>(a, blockIdx.x * kLineTile, blockIdx.y, blockIdx.z,
                           reinterpret_cast<float2*>(smem_raw));
+}
+
+// Register-direct variant (no shared memory): one warp per kRegCols adjacent
+// columns, see line_reg_group.  Used for radix <= 6.
+__host__ __device__ constexpr int line_reg_min_blocks(int R) { return R <= 4 ? 8 : 5; }
+
+template <int R, bool HALF>
+__global__ void __launch_bounds__(128, line_reg_min_blocks(R)) line_reg_kernel(const LineArgs<float> a,
+                                                                             int vec) {
+  const int lane = threadIdx.x & 31;
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int ncg = (a.ncol + kRegCols - 1) / kRegCols;
+  if (w >= (long long)ncg * a.nother * a.nbatch) return;        // warp-uniform; no barriers
+  const int cg = (int)(w % ncg);
+  const int o = (int)((w / ncg) % a.nother);
+  const int bb = (int)(w / ((long long)ncg * a.nother));
+  line_reg_group<R, HALF>(a, cg * kRegCols, o, bb, vec != 0, lane);
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <int R>
+static void launch_reg_r(LineArgs<float> a, cudaStream_t s) {
+  const int ncg = (a.ncol + kRegCols - 1) / kRegCols;
+  const long long warps = (long long)ncg * a.nother * a.nbatch;
+  const int threads = a.threads > 0 && a.threads <= 128 ? a.threads : 128;
+  const unsigned grid = (unsigned)((warps + threads / 32 - 1) / (threads / 32));
+  // 16-byte row accesses: every row start of every group is a multiple of 16 bytes
+  const bool even = a.in_bs % 2 == 0 && a.in_os % 2 == 0 && a.in_ls % 2 == 0 &&
+                    a.out_bs % 2 == 0 && a.out_os % 2 == 0 && a.out_ls % 2 == 0;
+  const int vec = even && aligned16(a.in) && aligned16(a.out) ? 1 : 0;
+  a.chi_vec = a.chi != nullptr && aligned16(a.chi) && a.chi_os % 2 == 0 && a.chi_ls % 2 == 0;
+  a.addend_vec = a.addend != nullptr && aligned16(a.addend);
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
+  const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
+  if (half) line_reg_kernel<R, true><<<grid, threads, 0, s>>>(a, vec);
+  else line_reg_kernel<R, false><<<grid, threads, 0, s>>>(a, vec);
 }
 
 template <int R>
@@ -100,12 +145,12 @@ static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
   if (N % 32 != 0 || a.in_cs != 1 || a.out_cs != 1) return false;
   if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
   switch (N / 32) {
-    case 1: launch_warp_r<1>(a, s); return true;
-    case 2: launch_warp_r<2>(a, s); return true;
-    case 3: launch_warp_r<3>(a, s); return true;
-    case 4: launch_warp_r<4>(a, s); return true;
-    case 5: launch_warp_r<5>(a, s); return true;
-    case 6: launch_warp_r<6>(a, s); return true;
+    case 1: launch_reg_r<1>(a, s); return true;
+    case 2: launch_reg_r<2>(a, s); return true;
+    case 3: launch_reg_r<3>(a, s); return true;
+    case 4: launch_reg_r<4>(a, s); return true;
+    case 5: launch_reg_r<5>(a, s); return true;
+    case 6: launch_reg_r<6>(a, s); return true;
     case 8: launch_warp_r<8>(a, s); return true;
     case 10: launch_warp_r<10>(a, s); return true;
     case 12: launch_warp_r<12>(a, s); return true;

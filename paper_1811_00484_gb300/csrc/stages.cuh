@@ -161,6 +161,146 @@ __device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0,
   }
 }
 
+// Columns per warp of the register-direct line stage: four c64 columns are one
+// 32-byte sector of a row.
+constexpr int kRegCols = 4;
+
+// One group of kRegCols adjacent columns of strided lines (an x or y stage),
+// transformed by one warp straight from and to global memory, no shared
+// memory: lane l holds rows l + 32 j (natural order) of every column, or rows
+// k1 + R brev5(l) (the lane FFT's bit-reversed order) on the frequency side.
+// Each row access moves the group's 32 contiguous bytes, two 16-byte accesses
+// when `vec` (the caller has checked that every row of the group starts on a
+// 16-byte boundary), one 8-byte access per column otherwise.  HALF: forward
+// from N/2 loaded points, or inverse cropped to N/2 stored points.
+template <int R, bool HALF>
+__device__ __forceinline__ void line_reg_group(const LineArgs<float>& a, int c0, int o, int bb,
+                                               bool vec, int lane) {
+  using C = float2;
+  constexpr int N = 32 * R;
+  constexpr int NC = kRegCols;
+  constexpr int NH = HALF ? (R + 1) / 2 : R;     // natural-order rows held per lane
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // warp-uniform
+  if (a.prof != nullptr && c0 == 0 && o == 0 && lane == 0) atomicAdd(a.prof, a.prof_batch_bytes);
+  const int ncols = min(NC, a.ncol - c0);
+  const bool v4 = vec && ncols == NC;
+  const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                       ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                       : 1.f;
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, a.roots, N);
+  const int br = brev5(lane);
+  C v[NC][R];
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
+  C* out = a.out + bb * a.out_bs + o * a.out_os + (long long)c0;
+  auto load_row = [&](int p, int j) {
+    const C* src = in + (long long)p * a.in_ls;
+    if (v4) {
+      const float4 x0 = *reinterpret_cast<const float4*>(src);
+      const float4 x1 = *reinterpret_cast<const float4*>(src + 2);
+      v[0][j] = make_float2(x0.x, x0.y);
+      v[1][j] = make_float2(x0.z, x0.w);
+      v[2][j] = make_float2(x1.x, x1.y);
+      v[3][j] = make_float2(x1.z, x1.w);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c][j] = c < ncols ? src[c] : make_float2(0.f, 0.f);
+    }
+  };
+  // kRegCols values of an array laid out like a row of the group (chi, addend)
+  auto load4 = [&](const C* src, bool wide, C* x) {
+    if (wide) {
+      const float4 x0 = *reinterpret_cast<const float4*>(src);
+      const float4 x1 = *reinterpret_cast<const float4*>(src + 2);
+      x[0] = make_float2(x0.x, x0.y);
+      x[1] = make_float2(x0.z, x0.w);
+      x[2] = make_float2(x1.x, x1.y);
+      x[3] = make_float2(x1.z, x1.w);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] = c < ncols ? src[c] : make_float2(0.f, 0.f);
+    }
+  };
+  const bool chi4 = v4 && a.chi_vec;
+  auto store_row = [&](int p, int j) {
+    C* dst = out + (long long)p * a.out_ls;
+    if (v4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0][j].x, v[0][j].y, v[1][j].x, v[1][j].y);
+      *reinterpret_cast<float4*>(dst + 2) = make_float4(v[2][j].x, v[2][j].y, v[3][j].x, v[3][j].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < ncols) dst[c] = v[c][j];
+    }
+  };
+  if (!a.inverse) {
+#pragma unroll
+    for (int j = 0; j < NH; ++j) {
+      const int p = lane + 32 * j;
+      if (p < a.lin) {
+        load_row(p, j);
+        if (a.flags & (PRO_RSCALE | PRO_CONJ | PRO_CHI)) {
+          C ch[NC];
+          if (a.flags & PRO_CHI) load4(a.chi + o * a.chi_os + (long long)p * a.chi_ls + c0, chi4, ch);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            C x = v[c][j];
+            if (a.flags & PRO_RSCALE) x = rs * x;
+            if (a.flags & PRO_CONJ) x = conjg(x);
+            if (a.flags & PRO_CHI) x = ch[c] * x;
+            v[c][j] = x;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c][j] = make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) warp_fft_fwd<C, float, R, HALF>(v[c], lc, a.roots, N);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+      const int p = k1 + R * br;
+      if (p < a.lout) store_row(p, k1);
+    }
+  } else {
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) load_row(k1 + R * br, k1);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) warp_fft_inv<C, float, R, HALF>(v[c], lane, lc, a.roots, N);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) {
+      const int p = lane + 32 * j;
+      if (p < a.lout) {
+        if (a.flags & (EPI_CONJ | EPI_SUB | EPI_ADD)) {
+          C ch[NC], ad[NC];
+          if (a.flags & (EPI_SUB | EPI_ADD)) {
+            if (a.flags & EPI_CHI) load4(a.chi + o * a.chi_os + (long long)p * a.chi_ls + c0, chi4, ch);
+            load4(a.addend + bb * a.out_bs + o * a.out_os + (long long)c0 + (long long)p * a.out_ls,
+                  v4 && a.addend_vec, ad);
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            C x = a.scale * v[c][j];
+            if (a.flags & EPI_CONJ) x = conjg(x);
+            if (a.flags & (EPI_SUB | EPI_ADD)) {
+              if (a.flags & EPI_CHI) x = ch[c] * x;
+              C w = ad[c];
+              if (a.flags & EPI_RSCALE) w = rs * w;
+              x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+            }
+            v[c][j] = x;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[c][j] = a.scale * v[c][j];
+        }
+        store_row(p, j);
+      }
+    }
+  }
+}
+
 // Slot of z-frequency k in a row of the rebuilt half fibre: one padding slot
 // every 8 entries, so the lanes' folded, bit-reversed frequencies (stride R)
 // fall in different banks (at most 2-way for the radices used, 4-way at R=10).

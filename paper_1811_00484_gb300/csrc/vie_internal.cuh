@@ -116,6 +116,7 @@ template <typename T> struct LineArgs {
   long long in_bs, in_os, in_ls, in_cs;
   long long out_bs, out_os, out_ls, out_cs;
   long long chi_os, chi_ls, chi_cs;    // chi index = o*chi_os + p*chi_ls + c*chi_cs
+  int chi_vec, addend_vec;             // chi / addend rows allow 16-byte accesses
   int batch_per_rhs;                   // batches per RHS (3 components) for `active`
   const int* active;                   // per-RHS flag (nullptr = all active)
   int threads;                         // CTA size of the register-path kernel (0 = 256)
