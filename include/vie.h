@@ -106,6 +106,10 @@ typedef struct vie_op_info_t {
     size_t slab_bytes;           /* c64 slab cores core x1 U1[k1,:] for the
                                     P1/2+1 rows k1 (formed at setup, reused by
                                     every matvec)                               */
+    size_t rebuild_scratch_bytes;/* c64 scratch into which every Tucker matvec
+                                    rebuilds the half fibres of a chunk of k1
+                                    (at most 64 MiB; 0 when the grid takes the
+                                    shared-memory path, which rebuilds on chip) */
     size_t uncompressed_bytes;   /* six c64 spectra, 6 P1 P2 P3 x 8 bytes       */
     size_t workspace_bytes;      /* scratch currently held                      */
     int has_uncompressed;        /* VIE_STORE_UNCOMPRESSED was given            */
@@ -206,7 +210,7 @@ int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
  * needs to start at zero: every call overwrites what it reads.
  * The first call on each device looks up the scratch address (with that
  * device current); make that first call before any stream capture.
- * All calls share the one array, so
+ * All calls share the one array (and the operator's rebuild scratch), so
  * calls that overlap on the GPU (different streams, or concurrent host
  * threads) race; serialise them.  J, Y: device [B][3][n1][n2][n3] c64.
  */
@@ -291,7 +295,7 @@ int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* ou
  * Benchmark instrumentation (no counterpart in the paper).  Between
  * vie_profile_start(mask) and vie_profile_stop() every launch of the kernel
  * families selected by `mask` (bit f = family f in the order line_x, line_y,
- * fused_tucker, fused_stored, line_iy, line_ix, slab_cores, arnoldi_dots,
+ * fused_tucker, fused_stored, line_iy, line_ix, tucker_rebuild, arnoldi_dots,
  * arnoldi_update, arnoldi_small, fp64_vector, setup; ~0u = all) is
  * bracketed by CUDA events on the stream it runs on
  * (inside CUDA graphs as event nodes read after each replay), and kernels

@@ -53,7 +53,7 @@ class Grid(ctypes.Structure):
 class OpInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("P", ctypes.c_int * 3), ("ranks", (ctypes.c_int * 3) * 6),
                 ("tucker_bytes", ctypes.c_size_t), ("tucker_bytes_full", ctypes.c_size_t),
-                ("slab_bytes", ctypes.c_size_t),
+                ("slab_bytes", ctypes.c_size_t), ("rebuild_scratch_bytes", ctypes.c_size_t),
                 ("uncompressed_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("has_uncompressed", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int)]
@@ -201,7 +201,7 @@ class Operator:
         return {"n": tuple(inf.n), "P": tuple(inf.P),
                 "ranks": [tuple(inf.ranks[c]) for c in range(6)],
                 "tucker_bytes": inf.tucker_bytes, "tucker_bytes_full": inf.tucker_bytes_full,
-                "slab_bytes": inf.slab_bytes,
+                "slab_bytes": inf.slab_bytes, "rebuild_scratch_bytes": inf.rebuild_scratch_bytes,
                 "uncompressed_bytes": inf.uncompressed_bytes,
                 "workspace_bytes": inf.workspace_bytes,
                 "has_uncompressed": bool(inf.has_uncompressed), "max_batch": inf.max_batch,
@@ -317,7 +317,7 @@ class Operator:
 
 
 PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy", "line_ix",
-                    "slab_cores", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
+                    "tucker_rebuild", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
                     "setup")
 
 

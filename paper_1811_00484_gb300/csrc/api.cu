@@ -168,6 +168,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   r.tucker_bytes = half * sizeof(float2);
   r.tucker_bytes_full = fullf * sizeof(float2);
   r.slab_bytes = 6 * op->slab_stride * sizeof(float2);
+  r.rebuild_scratch_bytes = (size_t)op->oct_k1 * op->H[1] * 6 * op->H[2] * sizeof(float2);
   r.uncompressed_bytes = 6ull * op->P[0] * op->P[1] * op->P[2] * sizeof(float2);
   r.workspace_bytes = op->ws.bytes + op->solve_ws.bytes;
   r.has_uncompressed = op->spec32 != nullptr;
@@ -358,6 +359,12 @@ int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* ou
 void vie_destroy(vie_op* op) {
   if (!op) return;
   solver_release(op);
+  if (op->rb_stream) {
+    cudaStreamSynchronize(op->rb_stream);
+    cudaStreamDestroy(op->rb_stream);
+  }
+  if (op->rb_fork) cudaEventDestroy(op->rb_fork);
+  if (op->rb_join) cudaEventDestroy(op->rb_join);
   for (int c = 0; c < 6; ++c) {
     TuckerComp& tc = op->comp[c];
     cudaFree(tc.core32);
@@ -366,9 +373,11 @@ void vie_destroy(vie_op* op) {
       cudaFree(tc.U32[q]);
       cudaFree(tc.U64[q]);
     }
+    cudaFree(tc.U3t32);
   }
   cudaFree(op->slab32);
   cudaFree(op->slab64);
+  cudaFree(op->oct32);
   cudaFree(op->spec32);
   cudaFree(op->spec64);
   for (int q = 0; q < 3; ++q) {

@@ -1,17 +1,24 @@
-// Fused z-axis FFT, Tucker rebuild, voxel-wise product and inverse z-FFT:
-// the element-wise product of the matvec (Section V.B, Table II) done with
-// the components decompressed on chip instead of into a buffer.
+// Fused z-axis FFT, voxel-wise product and inverse z-FFT: the element-wise
+// product of the matvec (Section V.B, Table II) with the components rebuilt
+// from their Tucker form at every matvec.
 //
-// The rebuild follows eq. (13) in two stages:
-//   slab cores   S_c[k1] = core_c x1 U1_c[k1, :]            (r2 x r3)
+// The rebuild follows eq. (13) in three stages:
+//   slab cores   S_c[k1] = core_c x1 U1_c[k1, :]            (r2 x r3, once, at setup)
 //   one fibre    G_c[k1, k2, k3] = sum_g ( U2_c[k2, :] S_c[k1] )[g] U3_c[k3, g]
 // The spectrum of every component is even or odd along each axis
 // (G_c[P - k] = s G_c[k], s = -1 when the component is odd in that
-// coordinate), and so are the HOSVD factors of its unfoldings.  One CTA
-// therefore rebuilds the fibre of (k1, k2) once, for k3 <= P3/2, and uses it,
-// with signs, for the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2) of every
-// right-hand side.  The stored (uncompressed) variant reads the six spectra
-// from memory instead.
+// coordinate), and so are the HOSVD factors of its unfoldings.  Only the half
+// fibres k3 <= P3/2 of the octant k1 <= P1/2, k2 <= P2/2 are rebuilt, and
+// each serves, with signs, the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2)
+// of every right-hand side.  On the register path the half fibres of a chunk
+// of k1 are rebuilt by octant_kernel into an FP32 scratch (one k1 chunk at a
+// time, so the scratch stays a small fraction of the uncompressed spectra),
+// and one CTA per (k1, k2) mirror group copies its 6 x (P3/2 + 1) values to
+// shared memory; the multi-grid and shared-memory variants rebuild the fibre
+// in the CTA.  The stored (uncompressed) variant reads the six spectra from
+// memory instead.
+#include <algorithm>
+
 #include "stages.cuh"
 
 namespace vie {
@@ -150,7 +157,75 @@ __host__ __device__ constexpr int fused_min_blocks(int R) {
 template <int R, bool STORED>
 __global__ void __launch_bounds__(128, fused_min_blocks(R)) fused_warp_kernel(const FusedArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_warp_group<R, STORED>(a, blockIdx.x, reinterpret_cast<float2*>(smem_raw));
+  fused_warp_group<R, STORED>(a, a.g0 + blockIdx.x, reinterpret_cast<float2*>(smem_raw));
+}
+
+// Rebuild of the half fibres of eq. (13) for k1 in [k1a, k1a + gridDim.y), every
+// k2 and k3 <= P3/2, into out[k1 - k1a][k2][c][k3]:
+//   W_c[k2, q]      = sum_b U2_c[k2, b] S_c[k1][b, q]          (S = slab core)
+//   G_c[k1, k2, k3] = sum_q W_c[k2, q] U3_c[k3, q]
+// One CTA per (k1, kOctK2 values of k2).  Each thread keeps the kOctK2 values
+// of one (c, q) or (c, k3) in registers, so every factor entry it loads serves
+// kOctK2 independent multiply-adds; U3 is read transposed (consecutive k3 at
+// consecutive addresses) and the output rows (k3 fastest) are written
+// contiguously.
+constexpr int kOctK2 = 8;
+
+struct OctArgs {
+  const CompMeta<float>* meta;
+  int r2max, r3max, H2, H3;
+  int k1a;
+  float2* out;
+};
+
+__global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* W = reinterpret_cast<float2*>(smem_raw);     // [6][r3max][kOctK2]
+  __shared__ CompMeta<float> meta[6];
+  if (threadIdx.x < 6) meta[threadIdx.x] = a.meta[threadIdx.x];
+  __syncthreads();
+  const int k1l = blockIdx.y, k1 = a.k1a + k1l;
+  const int k2_0 = blockIdx.x * kOctK2;
+  const int nk2 = min(kOctK2, a.H2 - k2_0);
+  const int r23 = a.r2max * a.r3max;
+  for (int it = threadIdx.x; it < 6 * a.r3max; it += blockDim.x) {
+    const int c = it / a.r3max, q = it - c * a.r3max;
+    const CompMeta<float>& m = meta[c];
+    float2 acc[kOctK2];
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t) acc[t] = make_float2(0.f, 0.f);
+    if (q < m.r3) {
+      const float2* S = m.slab + (long long)k1 * r23 + q;
+      const float2* u2 = m.U2 + (long long)k2_0 * m.r2;
+      for (int b = 0; b < m.r2; ++b) {
+        const float2 sv = S[b * a.r3max];
+#pragma unroll
+        for (int t = 0; t < kOctK2; ++t)
+          if (t < nk2) acc[t] = cmadd(u2[t * m.r2 + b], sv, acc[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t) W[it * kOctK2 + t] = acc[t];
+  }
+  __syncthreads();
+  float2* out = a.out + ((long long)k1l * a.H2 + k2_0) * 6 * a.H3;
+  for (int it = threadIdx.x; it < 6 * a.H3; it += blockDim.x) {
+    const int c = it / a.H3, kk = it - c * a.H3;
+    const CompMeta<float>& m = meta[c];
+    const float2* u3t = m.U3t + kk;           // U3_c[kk, q] at u3t[q * H3]
+    const float2* w = W + c * a.r3max * kOctK2;
+    float2 acc[kOctK2];
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int q = 0; q < m.r3; ++q) {
+      const float2 u = u3t[(long long)q * a.H3];
+#pragma unroll
+      for (int t = 0; t < kOctK2; ++t) acc[t] = cmadd(w[q * kOctK2 + t], u, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t)
+      if (t < nk2) out[(long long)t * 6 * a.H3 + it] = acc[t];
+  }
 }
 
 template <int R, bool STORED>
@@ -160,8 +235,35 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   a.prof = prof_bytes(fam);
   a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);
   a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(float2) : 0ull;
-  ProfScope ps(fam, s);
-  fused_warp_kernel<R, STORED><<<a.H1 * a.H2, 128, smem, s>>>(a);
+  if (STORED || a.octant == nullptr) {
+    ProfScope ps(fam, s);
+    a.g0 = 0;
+    fused_warp_kernel<R, STORED><<<a.H1 * a.H2, 128, smem, s>>>(a);
+    return;
+  }
+  // Tucker path: per chunk of k1, rebuild the half fibres (chunk 0 may already be
+  // rebuilt, see matvec_run), then the groups of the chunk
+  const int chunk = a.oct_chunk;
+  OctArgs o;
+  o.meta = a.meta;
+  o.r2max = a.r2max;
+  o.r3max = a.r3max;
+  o.H2 = a.H2;
+  o.H3 = a.H3;
+  o.out = const_cast<float2*>(a.octant);
+  const size_t osmem = (size_t)kOctK2 * 6 * a.r3max * sizeof(float2);
+  for (int k1a = 0; k1a < a.H1; k1a += chunk) {
+    const int nk1 = std::min(chunk, a.H1 - k1a);
+    o.k1a = k1a;
+    if (k1a > 0 || !a.oct_first_ready) {
+      ProfScope ps(PF_REBUILD, s);
+      octant_kernel<<<dim3((a.H2 + kOctK2 - 1) / kOctK2, nk1), 256, osmem, s>>>(o);
+    }
+    a.oct_k1a = k1a;
+    a.g0 = k1a * a.H2;
+    ProfScope ps(fam, s);
+    fused_warp_kernel<R, STORED><<<nk1 * a.H2, 128, smem, s>>>(a);
+  }
 }
 
 template <bool STORED>
@@ -234,7 +336,7 @@ vie::SlabArgs<T> make_slab_args(const vie_op* op) {
   a.slab_stride = (long long)op->slab_stride;
   a.r2max = op->rmax[1];
   a.r3max = op->rmax[2];
-  a.prof = prof_bytes(PF_SLAB);
+  a.prof = prof_bytes(PF_REBUILD);
   a.prof_launch_bytes = 6ull * op->slab_stride * sizeof(cx<T>);
   return a;
 }
@@ -243,7 +345,7 @@ template <typename T>
 int launch_slab_cores(const vie_op* op, cudaStream_t s) {
   vie::SlabArgs<T> a = make_slab_args<T>(op);
   dim3 grid(op->H[0], 6);
-  ProfScope ps(PF_SLAB, s);
+  ProfScope ps(PF_REBUILD, s);
   vie::slab_core_kernel<T><<<grid, 256, 0, s>>>(a);
   return VIE_OK;
 }
@@ -287,10 +389,34 @@ vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool sto
   return a;
 }
 
+int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
+  vie::OctArgs o;
+  o.meta = reinterpret_cast<const CompMeta<float>*>(op->meta);
+  o.r2max = op->rmax[1];
+  o.r3max = op->rmax[2];
+  o.H2 = op->H[1];
+  o.H3 = op->H[2];
+  o.k1a = k1a;
+  o.out = op->oct32;
+  const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
+  const size_t osmem = (size_t)vie::kOctK2 * 6 * o.r3max * sizeof(float2);
+  ProfScope ps(PF_REBUILD, s);
+  vie::octant_kernel<<<dim3((o.H2 + vie::kOctK2 - 1) / vie::kOctK2, nk1), 256, osmem, s>>>(o);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "rebuild launch");
+}
+
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool first_chunk_ready) {
   vie::FusedArgs<T> a = make_fused_args<T>(op, data, B, stored, active);
+  if constexpr (sizeof(T) == 4) {
+    if (!stored && op->oct32 != nullptr) {
+      a.octant = op->oct32;
+      a.oct_chunk = op->oct_k1;
+      a.oct_first_ready = first_chunk_ready;
+    }
+  }
   if (stored) {
     if (a.spec == nullptr) {
       set_error("operator was built without VIE_STORE_UNCOMPRESSED");
@@ -308,6 +434,8 @@ int fused_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  // octant_kernel also holds the six metadata records in static shared memory
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");
 }
 
@@ -315,5 +443,5 @@ template vie::SlabArgs<float> make_slab_args<float>(const vie_op*);
 template vie::FusedArgs<float> make_fused_args<float>(const vie_op*, float2*, int, bool, const int*);
 template int launch_slab_cores<float>(const vie_op*, cudaStream_t);
 template int launch_slab_cores<double>(const vie_op*, cudaStream_t);
-template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t);
-template int launch_fused<double>(const vie_op*, double2*, int, bool, const int*, cudaStream_t);
+template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t, bool);
+template int launch_fused<double>(const vie_op*, double2*, int, bool, const int*, cudaStream_t, bool);

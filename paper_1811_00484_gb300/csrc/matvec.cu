@@ -15,7 +15,7 @@
 
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
-                 cudaStream_t s);
+                 cudaStream_t s, bool first_chunk_ready);
 
 size_t workspace_bytes_for(const vie_op* op, int B) {
   const size_t n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
@@ -167,9 +167,23 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   const LineStages<T> st = make_line_stages<T>(op, ws, in, out, B, pro_flags, epi_flags, chi,
                                                addend, active, rscale, rscale_stride);
   C* T2 = const_cast<C*>(st.s[1].out);
+  // FP32 Tucker path on the register kernels: the first k1 chunk of the rebuild
+  // does not read J, so it runs on the operator's side stream beside the x and
+  // y stages and is joined before the fused kernel
+  bool pre = false;
+  if constexpr (sizeof(T) == 4) {
+    if (!stored && op->oct32 != nullptr && op->rb_stream != nullptr) {
+      VIE_CUDA(cudaEventRecord(op->rb_fork, s));
+      VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
+      VIE_TRY(launch_octant(op, 0, op->rb_stream));
+      VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
+      pre = true;
+    }
+  }
   launch_line_fft<T>(st.s[0], s);
   launch_line_fft<T>(st.s[1], s);
-  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s));
+  if (pre) VIE_CUDA(cudaStreamWaitEvent(s, op->rb_join, 0));
+  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s, pre));
   launch_line_fft<T>(st.s[2], s);
   launch_line_fft<T>(st.s[3], s);
   cudaError_t e = cudaGetLastError();

@@ -35,7 +35,7 @@ Profiler& prof() {
 thread_local std::vector<Pair>* t_capture_sink = nullptr;
 
 const char* kNames[VIE_PROF_FAMILIES] = {"line_x",    "line_y",   "fused_tucker", "fused_stored",
-                                         "line_iy",   "line_ix",  "slab_cores",   "arnoldi_dots",
+                                         "line_iy",   "line_ix",  "tucker_rebuild", "arnoldi_dots",
                                          "arnoldi_update", "arnoldi_small", "fp64_vector", "setup"};
 
 void harvest(std::vector<Pair>& v, Profiler& p, bool recycle) {

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "vie_internal.cuh"
+#include "warpfft.cuh"
 
 namespace {
 
@@ -569,6 +570,14 @@ static int compress_component(vie_op* op, int c, double tol, int rule, DeviceBuf
     VIE_TRY(dalloc(&tc.U32[q], u32.size() * sizeof(float2)));
     VIE_CUDA(cudaMemcpy(tc.U64[q], u64.data(), u64.size() * sizeof(double2), cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(tc.U32[q], u32.data(), u32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if (q == 2) {
+      // transposed copy: a warp rebuilding consecutive k3 reads consecutive addresses
+      std::vector<float2> t((size_t)r * h);
+      for (int i = 0; i < h; ++i)
+        for (int j = 0; j < r; ++j) t[(size_t)j * h + i] = u32[(size_t)i * r + j];
+      VIE_TRY(dalloc(&tc.U3t32, t.size() * sizeof(float2)));
+      VIE_CUDA(cudaMemcpy(tc.U3t32, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
   }
   VIE_CUDA(cudaStreamSynchronize(s));
   return VIE_OK;
@@ -586,10 +595,10 @@ static int finish_operator(vie_op* op) {
   CompMeta<double> m64[6];
   for (int c = 0; c < 6; ++c) {
     const TuckerComp& tc = op->comp[c];
-    m32[c] = CompMeta<float>{tc.U32[1], tc.U32[2], op->slab32 + c * op->slab_stride, tc.r[1],
-                             tc.r[2], tc.s[0], tc.s[1], tc.s[2]};
-    m64[c] = CompMeta<double>{tc.U64[1], tc.U64[2], op->slab64 + c * op->slab_stride, tc.r[1],
-                              tc.r[2], tc.s[0], tc.s[1], tc.s[2]};
+    m32[c] = CompMeta<float>{tc.U32[1], tc.U32[2], tc.U3t32, op->slab32 + c * op->slab_stride,
+                             tc.r[1], tc.r[2], tc.s[0], tc.s[1], tc.s[2]};
+    m64[c] = CompMeta<double>{tc.U64[1], tc.U64[2], nullptr, op->slab64 + c * op->slab_stride,
+                              tc.r[1], tc.r[2], tc.s[0], tc.s[1], tc.s[2]};
   }
   static_assert(sizeof(CompMeta<float>) == sizeof(CompMeta<double>), "meta layout");
   VIE_TRY(dalloc((char**)&op->meta, sizeof(m32) + sizeof(m64)));
@@ -600,6 +609,17 @@ static int finish_operator(vie_op* op) {
   // for the operator, so formed once here rather than at every matvec
   VIE_TRY(launch_slab_cores<float>(op, 0));
   VIE_TRY(launch_slab_cores<double>(op, 0));
+  // FP32 scratch for the per-matvec rebuild of the half fibres (register-path
+  // fused kernel): whole k1 planes of [H2][6][H3], as many as fit in kOctBudget
+  if (op->P[2] % 32 == 0 && vie::warp_fft_supported(op->P[2] / 32)) {
+    constexpr size_t kOctBudget = 64u << 20;
+    const size_t plane = (size_t)op->H[1] * 6 * op->H[2] * sizeof(float2);
+    op->oct_k1 = (int)std::max<size_t>(1, std::min<size_t>(op->H[0], kOctBudget / plane));
+    VIE_TRY(dalloc(&op->oct32, (size_t)op->oct_k1 * plane));
+    VIE_CUDA(cudaStreamCreateWithFlags(&op->rb_stream, cudaStreamNonBlocking));
+    VIE_CUDA(cudaEventCreateWithFlags(&op->rb_fork, cudaEventDisableTiming));
+    VIE_CUDA(cudaEventCreateWithFlags(&op->rb_join, cudaEventDisableTiming));
+  }
   VIE_CUDA(cudaDeviceSynchronize());
   return VIE_OK;
 }

@@ -38,6 +38,11 @@ template <typename T> struct FusedArgs {
   const cx<T>* spec;           // [6][P1][P2][P3] (stored)
   long long spec_stride;       // P1 * P2 * P3
   const int* active;           // per RHS, nullptr = all
+  const cx<T>* octant;         // rebuilt half fibres [k1 - oct_k1a][H2][6][H3] (nullptr: rebuild here)
+  int oct_k1a;                 // first k1 held in `octant`
+  int oct_chunk;               // k1 values per fill of `octant`
+  bool oct_first_ready;        // host: chunk 0 already rebuilt on the side stream (joined)
+  int g0;                      // group of the first CTA (k1 chunks)
   int lines_per_round;         // z-lines (x3 components) held in shared memory at once
   int ld;                      // shared-memory line stride
   unsigned long long* prof;    // profiler byte counter (nullptr = off)
@@ -334,12 +339,43 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
     atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
   }
 
+  // this warp's mirror line; with the half fibres rebuilt beforehand, the loads
+  // of its first active right-hand side are issued before the copy below so
+  // the two latencies overlap
+  const bool has_line = warp < nl;
+  const int ix = has_line ? warp / ny : 0, iy = has_line ? warp % ny : 0;
+  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
+  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
+  int b0 = 0;
+  if (a.active != nullptr)
+    while (b0 < a.B && a.active[b0] == 0) ++b0;
+  const bool pre = !STORED && a.octant != nullptr && has_line && b0 < a.B;
+  C v[3][R];
+  if (pre) {
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const C* src = a.data + (long long)(b0 * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < (R + 1) / 2; ++j) {
+        const int p = lane + 32 * j;
+        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+      }
+    }
+  }
+
   const int GS = ghalf_slot(H3 - 1) + 1;   // padded row length of the half fibre
   C* roots = smem;
   C* ghalf = roots + P3;               // [6][GS]
   C* wv = ghalf + 6 * GS;              // [6][r3max]
   for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
-  if (!STORED) {
+  if (!STORED && a.octant != nullptr) {
+    // the group's half fibres, rebuilt for this matvec by octant_kernel
+    const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it - c * H3;
+      ghalf[c * GS + ghalf_slot(kk)] = src[it];
+    }
+  } else if (!STORED) {
     for (int it = tid; it < 6 * a.r3max; it += nth) {
       const int c = it / a.r3max, gm = it % a.r3max;
       const CompMeta<float> m = a.meta[c];
@@ -354,36 +390,36 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
     __syncthreads();
     for (int it = tid; it < 6 * H3; it += nth) {
       const int c = it / H3, kk = it % H3;
-      const CompMeta<float> m = a.meta[c];
-      const C* u3 = m.U3 + (long long)kk * m.r3;
+      const CompMeta<float>& m = a.meta[c];
+      const C* u3t = m.U3t + kk;              // U3_c[kk, q] at u3t[q * H3]: coalesced
       const C* w = wv + c * a.r3max;
       C acc = make_float2(0.f, 0.f);
-      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3[q], acc);
+#pragma unroll 4
+      for (int q = 0; q < m.r3; ++q) acc = cmadd(w[q], u3t[(long long)q * H3], acc);
       ghalf[c * GS + ghalf_slot(kk)] = acc;
     }
   }
   __syncthreads();
-  if (warp >= nl) return;                  // no block barrier follows
+  if (!has_line) return;                   // no block barrier follows
 
-  const int ix = warp / ny, iy = warp % ny;
-  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
   const int br = brev5(lane);
   LaneConsts<C, float, R> lc;
   lc.init(lane, roots, P3);
-  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
-  for (int b = 0; b < a.B; ++b) {
+  for (int b = b0; b < a.B; ++b) {
     if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
-    C v[3][R];
+    if (!pre || b != b0) {
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+      for (int comp = 0; comp < 3; ++comp) {
+        const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
 #pragma unroll
-      for (int j = 0; j < (R + 1) / 2; ++j) {
-        const int p = lane + 32 * j;
-        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+        for (int j = 0; j < (R + 1) / 2; ++j) {
+          const int p = lane + 32 * j;
+          v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+        }
       }
-      warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
     }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int kk = q + R * br;                       // z-frequency held in register q

@@ -76,7 +76,7 @@ enum {
 // kernel-family profiler (profiler.cu)
 // ---------------------------------------------------------------------------
 enum {
-  PF_LINE_X = 0, PF_LINE_Y, PF_FUSED_TUCKER, PF_FUSED_STORED, PF_LINE_IY, PF_LINE_IX, PF_SLAB,
+  PF_LINE_X = 0, PF_LINE_Y, PF_FUSED_TUCKER, PF_FUSED_STORED, PF_LINE_IY, PF_LINE_IX, PF_REBUILD,
   PF_DOTS, PF_UPDATE, PF_SMALL, PF_FP64, PF_SETUP, VIE_PROF_FAMILIES
 };
 struct ProfEventPair {
@@ -135,6 +135,7 @@ struct TuckerComp {
   int s[3];            // parity sign of the spectrum along each axis
   float2* core32 = nullptr;  double2* core64 = nullptr;   // [r1][r2][r3]
   float2* U32[3] = {};       double2* U64[3] = {};        // half factors [H_q][r_q]
+  float2* U3t32 = nullptr;                                 // U3 half factor transposed [r3][H3]
   std::vector<double> sigma[3];                            // H_q singular values
 };
 
@@ -159,6 +160,14 @@ struct vie_op {
   // slab cores S_c[k1] = core_c x1 U1_c[k1, :] (mode 1 of eq. (13)), formed at setup
   float2* slab32 = nullptr;  double2* slab64 = nullptr;
   size_t slab_stride;        // elements per component: H1 * rmax2 * rmax3
+  // per-matvec rebuild of the half fibres (FP32 Tucker path): scratch for
+  // oct_k1 values of k1 at a time, [oct_k1][H2][6][H3], rewritten by every matvec
+  float2* oct32 = nullptr;
+  int oct_k1 = 0;
+  // the first chunk's rebuild does not depend on J: it runs on this stream
+  // beside the x and y stages and is joined before the fused kernel
+  cudaStream_t rb_stream = nullptr;
+  cudaEvent_t rb_fork = nullptr, rb_join = nullptr;
   // stored spectra (optional)
   float2* spec32 = nullptr;  double2* spec64 = nullptr;
   FftPlan plan[3];
@@ -177,6 +186,7 @@ struct vie_op {
 template <typename T> struct CompMeta {
   const cx<T>* U2;   // [H2][r2]
   const cx<T>* U3;   // [H3][r3]
+  const cx<T>* U3t;  // [r3][H3] (FP32 only: coalesced rebuild reads; nullptr in FP64)
   const cx<T>* slab; // [H1][r2][r3] (row stride rmax)
   int r2, r3;
   int s1, s2, s3;
@@ -227,6 +237,8 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
 size_t workspace_bytes_for(const vie_op* op, int B);
 
 template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
+// rebuild of the half fibres of k1 in [k1a, k1a + oct_k1) into op->oct32 (fused.cu)
+int launch_octant(const vie_op* op, int k1a, cudaStream_t s);
 
 // setup internals (setup.cu)
 int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,
