@@ -71,6 +71,10 @@ template <int W> __device__ __forceinline__ Pack<W> zpack() {
   return r;
 }
 
+__device__ __forceinline__ float2 shfl_xor32(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
 __device__ __forceinline__ float2 wsum32(float2 v) {
   for (int o = 16; o > 0; o >>= 1) {
     v.x += __shfl_down_sync(0xffffffffu, v.x, o);
@@ -83,7 +87,7 @@ __device__ __forceinline__ float2 wsum32(float2 v) {
 constexpr int kDotThreads = 128;
 constexpr int kDotPacks = 2;
 constexpr int kDotBlock = 4;
-constexpr int kMaxDotCtas = 1024;             // per right-hand side (bounds the partials)
+constexpr int kMaxDotCtas = 4096;             // per right-hand side (bounds the partials)
 // update: one pack per thread, basis vectors kUpdBlock at a time
 constexpr int kUpdThreads = 256;
 constexpr int kUpdBlock = 4;
@@ -95,7 +99,7 @@ constexpr int kUpdBlock = 4;
 template <int W>
 __global__ void __launch_bounds__(kDotThreads) dots_kernel(const float2* __restrict__ V,
                                                            const float2* __restrict__ w, int k, int B,
-                                                           long long N, int G, double2* partial,
+                                                           long long N, int G, int ps, double2* partial,
                                                            const int* active,
                                                            unsigned long long* prof,
                                                            unsigned long long prof_bytes) {
@@ -138,18 +142,30 @@ __global__ void __launch_bounds__(kDotThreads) dots_kernel(const float2* __restr
         }
         acc[u] = make_float2(ax, ay);
       }
-#pragma unroll
-      for (int u = 0; u < kDotBlock; ++u) {
-        const float2 s = wsum32(acc[u]);
-        if (lane == 0 && i0 + u <= k) red[warp][i0 + u] = red[warp][i0 + u] + make_double2(s.x, s.y);
-      }
+      // warp sums of the four accumulators in one butterfly (12 shuffles, not 40):
+      // halve the values each lane holds at xor 16 and 8, then finish at 4, 2, 1;
+      // lanes 8u .. 8u+7 end with the sum of acc[u]
+      static_assert(kDotBlock == 4, "butterfly below reduces four accumulators");
+      const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+      float2 k0 = h16 ? acc[2] : acc[0], k1 = h16 ? acc[3] : acc[1];
+      const float2 s0 = h16 ? acc[0] : acc[2], s1 = h16 ? acc[1] : acc[3];
+      k0 = k0 + shfl_xor32(s0, 16);
+      k1 = k1 + shfl_xor32(s1, 16);
+      float2 kv = h8 ? k1 : k0;
+      kv = kv + shfl_xor32(h8 ? k0 : k1, 8);
+      kv = kv + shfl_xor32(kv, 4);
+      kv = kv + shfl_xor32(kv, 2);
+      kv = kv + shfl_xor32(kv, 1);
+      const int u = lane >> 3;
+      if ((lane & 7) == 0 && i0 + u <= k)
+        red[warp][i0 + u] = red[warp][i0 + u] + make_double2(kv.x, kv.y);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= k; i += kDotThreads) {
     double2 s = red[0][i];
     for (int q = 1; q < NW; ++q) s = s + red[q][i];
-    partial[((long long)b * 129 + i) * G + cta] = s;
+    partial[((long long)b * ps + i) * G + cta] = s;
   }
 }
 
@@ -157,14 +173,14 @@ __global__ void __launch_bounds__(kDotThreads) dots_kernel(const float2* __restr
 // One CTA of kReduceThreads per (i, b).
 constexpr int kReduceThreads = 128;
 __global__ void __launch_bounds__(kReduceThreads) reduce_dots_kernel(const double2* partial, int k,
-                                                                     int G, const double* sig,
+                                                                     int G, int ps, const double* sig,
                                                                      double2* coef, double2* H,
                                                                      int m, int accumulate,
                                                                      const int* active) {
   const int b = blockIdx.y, i = blockIdx.x;
   if (!active[b]) return;
   __shared__ double2 red[kReduceThreads / 32];
-  const double2* p = partial + ((long long)b * 129 + i) * G;
+  const double2* p = partial + ((long long)b * ps + i) * G;
   double2 s = make_double2(0.0, 0.0);
   for (int c = threadIdx.x; c < G; c += kReduceThreads) s = s + p[c];
   s = wsum(s);
@@ -390,20 +406,34 @@ __global__ void __launch_bounds__(kThreads) norm32_kernel(const float2* v, long 
   }
 }
 
-// y = R^-1 g over the iters[b] columns of the rotated Hessenberg matrix
-__global__ void backsolve_kernel(const double2* H, const double2* g, double2* y, int m, int B,
-                                 const int* iters) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+// y = R^-1 g over the iters[b] columns of the rotated Hessenberg matrix, one
+// warp per right-hand side: the reciprocals of the diagonal are formed in
+// parallel first (an FP64 division is slow on GB300), then column by column
+// y_i = r_i / R_ii and the lanes update r_j -= R_ji y_i for j < i.
+__global__ void __launch_bounds__(128) backsolve_kernel(const double2* __restrict__ H,
+                                                        const double2* g, double2* y, int m, int B,
+                                                        const int* iters) {
+  __shared__ double2 r[4][129], rinv[4][128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * 4 + warp;
+  if (b >= B) return;                          // warp-uniform; no block barrier below
   const int kk = iters[b];
   const double2* gb = g + (long long)b * (m + 1);
+  const double2* Hb = H + (long long)b * m * (m + 1);   // column j at Hb + j (m + 1)
   double2* yb = y + (long long)b * 129;
-  for (int i = kk - 1; i >= 0; --i) {
-    double2 s = gb[i];
-    for (int j = i + 1; j < kk; ++j) s = s - H[((long long)b * m + j) * (m + 1) + i] * yb[j];
-    const double2 d = H[((long long)b * m + i) * (m + 1) + i];
+  for (int i = lane; i < kk; i += 32) {
+    r[warp][i] = gb[i];
+    const double2 d = Hb[(long long)i * (m + 1) + i];
     const double dd = abs2(d);
-    yb[i] = dd > 0.0 ? (1.0 / dd) * (s * conjg(d)) : make_double2(0.0, 0.0);
+    rinv[warp][i] = dd > 0.0 ? (1.0 / dd) * conjg(d) : make_double2(0.0, 0.0);
+  }
+  __syncwarp();
+  for (int i = kk - 1; i >= 0; --i) {
+    const double2 yi = r[warp][i] * rinv[warp][i];
+    if (lane == 0) yb[i] = yi;
+    const double2* col = Hb + (long long)i * (m + 1);
+    for (int jj = lane; jj < i; jj += 32) r[warp][jj] = r[warp][jj] - col[jj] * yi;
+    __syncwarp();
   }
 }
 
@@ -689,7 +719,7 @@ static size_t carve_bytes(int B, int m, long long N, int nchunk, int G, int Gu) 
   carve<double2>(p, (size_t)B * m);                   // sn
   carve<double2>(p, (size_t)B * (m + 1));             // g
   carve<double2>(p, (size_t)B * 129);                 // coef / y
-  carve<double2>(p, (size_t)B * 129 * G);             // partial dots
+  carve<double2>(p, (size_t)B * (m + 1) * G);         // partial dots
   carve<double>(p, (size_t)B * std::max(nchunk, Gu)); // norm partials
   for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm beta tol_abs rnorm bnorm
   carve<double>(p, (size_t)B * (m + 1));              // sig
@@ -711,7 +741,10 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   const int wide = (N % 2 == 0) ? 1 : 0;
   const int W = wide ? 2 : 1;
   const long long dtile = (long long)kDotThreads * kDotPacks * W;
-  const int G = (int)std::min<long long>((N + dtile - 1) / dtile, kMaxDotCtas);
+  // tiles per CTA: as few as the cap on CTAs allows, and the same for every CTA
+  const long long ntile = (N + dtile - 1) / dtile;
+  const long long per = (ntile + kMaxDotCtas - 1) / kMaxDotCtas;
+  const int G = (int)((ntile + per - 1) / per);
   const int Gu = (int)((N + (long long)kUpdThreads * W - 1) / ((long long)kUpdThreads * W));
   release_state(st);
   op->solver = nullptr;
@@ -752,7 +785,7 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->sn = carve<double2>(p, (size_t)B * m);
   st->g = carve<double2>(p, (size_t)B * (m + 1));
   st->coef = carve<double2>(p, (size_t)B * 129);
-  st->partial = carve<double2>(p, (size_t)B * 129 * st->G);
+  st->partial = carve<double2>(p, (size_t)B * (m + 1) * st->G);
   st->nrm_partial = carve<double>(p, (size_t)B * std::max(nc, st->Gu));
   st->nrm = carve<double>(p, B);
   carve<double>(p, B);
@@ -823,15 +856,15 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
     {
       ProfScope ps(PF_DOTS, s);
       if (st->wide)
-        dots_kernel<2><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, st->partial, mask,
+        dots_kernel<2><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, m + 1, st->partial, mask,
                                                           prof_bytes(PF_DOTS), (k + 2) * vec);
       else
-        dots_kernel<1><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, st->partial, mask,
+        dots_kernel<1><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, m + 1, st->partial, mask,
                                                           prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
-      reduce_dots_kernel<<<dim3(k + 1, B), kReduceThreads, 0, s>>>(st->partial, k, G, st->sig,
+      reduce_dots_kernel<<<dim3(k + 1, B), kReduceThreads, 0, s>>>(st->partial, k, G, m + 1, st->sig,
                                                                    st->coef, st->H, m, pass, mask);
     }
     {
@@ -871,7 +904,7 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
   VIE_TRY(join_givens(st, s));
   {
     ProfScope ps(PF_SMALL, s);
-    backsolve_kernel<<<(B + 63) / 64, 64, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
+    backsolve_kernel<<<(B + 3) / 4, 128, 0, s>>>(st->H, st->g, st->coef, m, B, st->iters);
     combine_kernel<<<grid, kThreads, 0, s>>>(st->V, st->d, st->coef, st->sig, m, B, N, st->iters);
   }
   // W = A d for the RHS still wanted
