@@ -238,7 +238,7 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   if (STORED || a.octant == nullptr) {
     ProfScope ps(fam, s);
     a.g0 = 0;
-    fused_warp_kernel<R, STORED><<<a.H1 * a.H2, 128, smem, s>>>(a);
+    launch_pdl(fused_warp_kernel<R, STORED>, dim3(a.H1 * a.H2), dim3(128), smem, s, a);
     return;
   }
   // Tucker path: per chunk of k1, rebuild the half fibres (chunk 0 may already be
@@ -262,7 +262,7 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
     a.oct_k1a = k1a;
     a.g0 = k1a * a.H2;
     ProfScope ps(fam, s);
-    fused_warp_kernel<R, STORED><<<nk1 * a.H2, 128, smem, s>>>(a);
+    launch_pdl(fused_warp_kernel<R, STORED>, dim3(nk1 * a.H2), dim3(128), smem, s, a);
   }
 }
 

@@ -123,8 +123,8 @@ static void launch_reg_r(LineArgs<float> a, cudaStream_t s) {
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
   const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
-  if (half) line_reg_kernel<R, true><<<grid, threads, 0, s>>>(a, vec);
-  else line_reg_kernel<R, false><<<grid, threads, 0, s>>>(a, vec);
+  launch_pdl(half ? line_reg_kernel<R, true> : line_reg_kernel<R, false>, dim3(grid), dim3(threads), 0,
+             s, a, vec);
 }
 
 template <int R>
@@ -136,8 +136,8 @@ static void launch_warp_r(LineArgs<float> a, cudaStream_t s) {
   const int threads = a.threads > 0 ? a.threads : 256;
   // half-length lines: forward from n = N/2 points, or inverse cropped to N/2
   const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
-  if (half) line_warp_kernel<R, true><<<grid, threads, smem, s>>>(a);
-  else line_warp_kernel<R, false><<<grid, threads, smem, s>>>(a);
+  launch_pdl(half ? line_warp_kernel<R, true> : line_warp_kernel<R, false>, grid, dim3(threads), smem,
+             s, a);
 }
 
 static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {

@@ -106,12 +106,14 @@ __global__ void __launch_bounds__(kDotThreads) dots_kernel(const float2* __restr
   constexpr int NW = kDotThreads / 32;
   constexpr int TILE = kDotThreads * kDotPacks * W;
   const int b = blockIdx.y, cta = blockIdx.x;
-  if (!active[b]) return;
-  if (prof != nullptr && cta == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   __shared__ double2 red[NW][129];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = lane; i <= k; i += 32) red[warp][i] = make_double2(0.0, 0.0);
   __syncwarp();
+  pdl_trigger();
+  pdl_wait();
+  if (!active[b]) return;
+  if (prof != nullptr && cta == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   const long long ntile = (N + TILE - 1) / TILE;
   const float2* wb = w + (long long)b * N;
   for (long long t = cta; t < ntile; t += G) {
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_dots_kernel(const doubl
                                                                      int m, int accumulate,
                                                                      const int* active) {
   const int b = blockIdx.y, i = blockIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (!active[b]) return;
   __shared__ double2 red[kReduceThreads / 32];
   const double2* p = partial + ((long long)b * ps + i) * G;
@@ -214,6 +218,8 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const float2* __res
                                                              unsigned long long* prof,
                                                              unsigned long long prof_bytes) {
   const int b = blockIdx.y, cta = blockIdx.x;
+  pdl_trigger();
+  pdl_wait();
   if (!mask[b]) return;
   if (prof != nullptr && cta == 0 && threadIdx.x == 0) atomicAdd(prof, prof_bytes);
   __shared__ float2 c[129];
@@ -855,28 +861,22 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
     const int mode = (pass == 0 && passes > 1) ? UPD_DGKS : UPD_FINAL;
     {
       ProfScope ps(PF_DOTS, s);
-      if (st->wide)
-        dots_kernel<2><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, m + 1, st->partial, mask,
-                                                          prof_bytes(PF_DOTS), (k + 2) * vec);
-      else
-        dots_kernel<1><<<dim3(G, B), kDotThreads, 0, s>>>(st->V, w, k, B, N, G, m + 1, st->partial, mask,
-                                                          prof_bytes(PF_DOTS), (k + 2) * vec);
+      launch_pdl(st->wide ? dots_kernel<2> : dots_kernel<1>, dim3(G, B), dim3(kDotThreads), 0, s,
+                 (const float2*)st->V, (const float2*)w, k, B, N, G, m + 1, st->partial, mask,
+                 prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     {
       ProfScope ps(PF_SMALL, s);
-      reduce_dots_kernel<<<dim3(k + 1, B), kReduceThreads, 0, s>>>(st->partial, k, G, m + 1, st->sig,
-                                                                   st->coef, st->H, m, pass, mask);
+      launch_pdl(reduce_dots_kernel, dim3(k + 1, B), dim3(kReduceThreads), 0, s,
+                 (const double2*)st->partial, k, G, m + 1, (const double*)st->sig, st->coef, st->H, m,
+                 pass, mask);
     }
     {
       ProfScope ps(PF_UPDATE, s);
-      if (st->wide)
-        update_kernel<2><<<dim3(Gu, B), kUpdThreads, 0, s>>>(
-            st->V, w, st->coef, st->sig, k, m, B, N, Gu, st->nrm_partial, st->ticket, mode, st->nrm,
-            st->again, mask, prof_bytes(PF_UPDATE), (k + 3) * vec);
-      else
-        update_kernel<1><<<dim3(Gu, B), kUpdThreads, 0, s>>>(
-            st->V, w, st->coef, st->sig, k, m, B, N, Gu, st->nrm_partial, st->ticket, mode, st->nrm,
-            st->again, mask, prof_bytes(PF_UPDATE), (k + 3) * vec);
+      launch_pdl(st->wide ? update_kernel<2> : update_kernel<1>, dim3(Gu, B), dim3(kUpdThreads), 0,
+                 s, (const float2*)st->V, w, (const double2*)st->coef, st->sig, k, m, B, N, Gu,
+                 st->nrm_partial, st->ticket, mode, st->nrm, st->again, mask,
+                 prof_bytes(PF_UPDATE), (k + 3) * vec);
     }
   }
   // the Givens step beside the next matvec

@@ -95,13 +95,15 @@ __device__ __forceinline__ void line_warp_tile(const LineArgs<float>& a, int c0,
   constexpr int TW = kLineTile;
   C* tile = smem;                  // element (row p, column c) at tile_slot(p, c)
   C* roots = smem + N * TW;
-  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  // prologue (tables only), then the preceding kernel's results
+  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
+  pdl_trigger();
+  pdl_wait();
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
   if (a.prof != nullptr && c0 == 0 && o == 0 && tid == 0) atomicAdd(a.prof, a.prof_batch_bytes);
   const int ncols = min(TW, a.ncol - c0);
-
-  for (int m = tid; m < N; m += nth) roots[m] = a.roots[m];
   const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
                        ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
                        : 1.f;
@@ -185,6 +187,11 @@ __device__ __forceinline__ void line_reg_group(const LineArgs<float>& a, int c0,
   constexpr int N = 32 * R;
   constexpr int NC = kRegCols;
   constexpr int NH = HALF ? (R + 1) / 2 : R;     // natural-order rows held per lane
+  // prologue (tables only), then the preceding kernel's results
+  LaneConsts<C, float, R> lc;
+  lc.init(lane, a.roots, N);
+  pdl_trigger();
+  pdl_wait();
   if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // warp-uniform
   if (a.prof != nullptr && c0 == 0 && o == 0 && lane == 0) atomicAdd(a.prof, a.prof_batch_bytes);
   const int ncols = min(NC, a.ncol - c0);
@@ -192,8 +199,6 @@ __device__ __forceinline__ void line_reg_group(const LineArgs<float>& a, int c0,
   const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
                        ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
                        : 1.f;
-  LaneConsts<C, float, R> lc;
-  lc.init(lane, a.roots, N);
   const int br = brev5(lane);
   C v[NC][R];
   const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)c0;
@@ -326,6 +331,7 @@ template <int R, bool STORED>
 __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int g, float2* smem) {
   using C = float2;
   constexpr int P3 = 32 * R;
+  constexpr int NLOAD = (R + 1) / 2;               // points lane + 32 j < P3 / 2 + 16
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int n3 = a.n3, H3 = a.H3;
@@ -333,49 +339,19 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
   const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
   const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
   const int nl = nx * ny;
-  if (a.prof != nullptr && g == 0 && tid == 0) {
-    unsigned long long nb = 0;
-    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
-    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
-  }
-
-  // this warp's mirror line; with the half fibres rebuilt beforehand, the loads
-  // of its first active right-hand side are issued before the copy below so
-  // the two latencies overlap
-  const bool has_line = warp < nl;
+  const bool has_line = warp < nl;                 // this warp's mirror line
   const int ix = has_line ? warp / ny : 0, iy = has_line ? warp % ny : 0;
   const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
   const long long line_off = ((long long)kx * a.P2 + ky) * n3;
-  int b0 = 0;
-  if (a.active != nullptr)
-    while (b0 < a.B && a.active[b0] == 0) ++b0;
-  const bool pre = !STORED && a.octant != nullptr && has_line && b0 < a.B;
-  C v[3][R];
-  if (pre) {
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const C* src = a.data + (long long)(b0 * 3 + comp) * a.comp_stride + line_off;
-#pragma unroll
-      for (int j = 0; j < (R + 1) / 2; ++j) {
-        const int p = lane + 32 * j;
-        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
-      }
-    }
-  }
 
   const int GS = ghalf_slot(H3 - 1) + 1;   // padded row length of the half fibre
   C* roots = smem;
   C* ghalf = roots + P3;               // [6][GS]
   C* wv = ghalf + 6 * GS;              // [6][r3max]
+  // prologue: tables and factors only (no earlier kernel writes them)
   for (int m = tid; m < P3; m += nth) roots[m] = a.roots[m];
-  if (!STORED && a.octant != nullptr) {
-    // the group's half fibres, rebuilt for this matvec by octant_kernel
-    const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
-    for (int it = tid; it < 6 * H3; it += nth) {
-      const int c = it / H3, kk = it - c * H3;
-      ghalf[c * GS + ghalf_slot(kk)] = src[it];
-    }
-  } else if (!STORED) {
+  const bool rebuild_here = !STORED && a.octant == nullptr;
+  if (rebuild_here) {
     for (int it = tid; it < 6 * a.r3max; it += nth) {
       const int c = it / a.r3max, gm = it % a.r3max;
       const CompMeta<float> m = a.meta[c];
@@ -399,31 +375,61 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
       ghalf[c * GS + ghalf_slot(kk)] = acc;
     }
   }
+  pdl_trigger();
+  pdl_wait();
+
+  if (a.prof != nullptr && g == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
+  // the first active right-hand side's lines are loaded before the half fibres
+  // are copied, so the two latencies overlap
+  int b0 = 0;
+  if (a.active != nullptr)
+    while (b0 < a.B && a.active[b0] == 0) ++b0;
+  C v[3][R];
+  auto load_lines = [&](int b) {
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+#pragma unroll
+      for (int j = 0; j < NLOAD; ++j) {
+        const int p = lane + 32 * j;
+        v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  if (has_line && b0 < a.B) load_lines(b0);
+  if (!STORED && !rebuild_here) {
+    // the group's half fibres, rebuilt for this matvec by octant_kernel
+    const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it - c * H3;
+      ghalf[c * GS + ghalf_slot(kk)] = src[it];
+    }
+  }
   __syncthreads();
   if (!has_line) return;                   // no block barrier follows
 
   const int br = brev5(lane);
   LaneConsts<C, float, R> lc;
   lc.init(lane, roots, P3);
+  // mirror signs: the component (a, b) of the spectrum at the mirror point is
+  // s_a s_b times its half-fibre value, s_q = -1 along each mirrored axis, so
+  // Y = D G D J with D = diag(s_x, s_y, s_z)
+  const float sx = ix ? -1.f : 1.f, sy = iy ? -1.f : 1.f;
   for (int b = b0; b < a.B; ++b) {
     if (a.active != nullptr && a.active[b] == 0) continue;   // warp-uniform
-    if (!pre || b != b0) {
-#pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        const C* src = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-#pragma unroll
-        for (int j = 0; j < (R + 1) / 2; ++j) {
-          const int p = lane + 32 * j;
-          v[comp][j] = p < n3 ? src[p] : make_float2(0.f, 0.f);
-        }
-      }
-    }
+    if (b != b0) load_lines(b);
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) warp_fft_fwd<C, float, R, true>(v[comp], lc, roots, P3);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int kk = q + R * br;                       // z-frequency held in register q
       C gc[6];
+      C jx = v[0][q], jy = v[1][q], jz = v[2][q];
+      float sz = 1.f;
       if (STORED) {
         const long long off = ((long long)kx * a.P2 + ky) * P3 + kk;
 #pragma unroll
@@ -431,28 +437,34 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
       } else {
         const bool zm = 2 * kk > P3;
         const int fold = zm ? P3 - kk : kk;
+        sz = zm ? -1.f : 1.f;
+        const C* gp = ghalf + ghalf_slot(fold);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          int s = 1;
-          if (ix) s *= parity_sign(c, 0);
-          if (iy) s *= parity_sign(c, 1);
-          if (zm) s *= parity_sign(c, 2);
-          const C gv = ghalf[c * GS + ghalf_slot(fold)];
-          gc[c] = (s > 0) ? gv : make_float2(-gv.x, -gv.y);
-        }
+        for (int c = 0; c < 6; ++c) gc[c] = gp[c * GS];
+        jx = sx * jx;
+        jy = sy * jy;
+        jz = sz * jz;
       }
-      const C jx = v[0][q], jy = v[1][q], jz = v[2][q];
       // Y_a = sum_b G_ab J_b with G symmetric: xx xy xz / xy yy yz / xz yz zz
-      v[0][q] = gc[0] * jx + gc[1] * jy + gc[2] * jz;
-      v[1][q] = gc[1] * jx + gc[3] * jy + gc[4] * jz;
-      v[2][q] = gc[2] * jx + gc[4] * jy + gc[5] * jz;
+      const C yx = gc[0] * jx + gc[1] * jy + gc[2] * jz;
+      const C yy = gc[1] * jx + gc[3] * jy + gc[4] * jz;
+      const C yz = gc[2] * jx + gc[4] * jy + gc[5] * jz;
+      if (STORED) {
+        v[0][q] = yx;
+        v[1][q] = yy;
+        v[2][q] = yz;
+      } else {
+        v[0][q] = sx * yx;
+        v[1][q] = sy * yy;
+        v[2][q] = sz * yz;
+      }
     }
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       warp_fft_inv<C, float, R, true>(v[comp], lane, lc, roots, P3);
       C* dst = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
 #pragma unroll
-      for (int j = 0; j < (R + 1) / 2; ++j) {
+      for (int j = 0; j < NLOAD; ++j) {
         const int p = lane + 32 * j;
         if (p < n3) dst[p] = v[comp][j];
       }

@@ -73,6 +73,35 @@ enum {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start
+// while the kernel before it on the stream is still running, as soon as every
+// CTA of that kernel has executed pdl_trigger(); everything it does before
+// pdl_wait() must only read data that no earlier kernel writes (tables,
+// factors) and only write on-chip storage.  pdl_wait() returns once the
+// preceding kernel has completed and its memory is visible (immediately for a
+// kernel launched without the attribute).  Both are no-ops for the driver
+// outside such a launch, and neither waits on memory written by other CTAs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // kernel-family profiler (profiler.cu)
 // ---------------------------------------------------------------------------
 enum {
