@@ -188,24 +188,20 @@ __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
   const int k2_0 = blockIdx.x * kOctK2;
   const int nk2 = min(kOctK2, a.H2 - k2_0);
   const int r23 = a.r2max * a.r3max;
-  for (int it = threadIdx.x; it < 6 * a.r3max; it += blockDim.x) {
-    const int c = it / a.r3max, q = it - c * a.r3max;
+  // W[c][q][t] = sum_b U2_c[k2_0 + t, b] S_c[k1][b, q]: one (c, q, t) per thread,
+  // t fastest (conflict-free stores)
+  for (int it = threadIdx.x; it < 6 * a.r3max * kOctK2; it += blockDim.x) {
+    const int t = it % kOctK2, cq = it / kOctK2;
+    const int c = cq / a.r3max, q = cq - c * a.r3max;
     const CompMeta<float>& m = meta[c];
-    float2 acc[kOctK2];
-#pragma unroll
-    for (int t = 0; t < kOctK2; ++t) acc[t] = make_float2(0.f, 0.f);
-    if (q < m.r3) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (q < m.r3 && t < nk2) {
       const float2* S = m.slab + (long long)k1 * r23 + q;
-      const float2* u2 = m.U2 + (long long)k2_0 * m.r2;
-      for (int b = 0; b < m.r2; ++b) {
-        const float2 sv = S[b * a.r3max];
-#pragma unroll
-        for (int t = 0; t < kOctK2; ++t)
-          if (t < nk2) acc[t] = cmadd(u2[t * m.r2 + b], sv, acc[t]);
-      }
+      const float2* u2 = m.U2 + (long long)(k2_0 + t) * m.r2;
+#pragma unroll 4
+      for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max], acc);
     }
-#pragma unroll
-    for (int t = 0; t < kOctK2; ++t) W[it * kOctK2 + t] = acc[t];
+    W[it] = acc;
   }
   __syncthreads();
   float2* out = a.out + ((long long)k1l * a.H2 + k2_0) * 6 * a.H3;

@@ -161,7 +161,8 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
 template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
-               const int* active, cudaStream_t s, const double* rscale, long long rscale_stride) {
+               const int* active, cudaStream_t s, const double* rscale, long long rscale_stride,
+               int mv_flags) {
   using C = cx<T>;
   const bool stored = (path == VIE_PATH_UNCOMPRESSED);
   const LineStages<T> st = make_line_stages<T>(op, ws, in, out, B, pro_flags, epi_flags, chi,
@@ -170,15 +171,19 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   // FP32 Tucker path on the register kernels: the first k1 chunk of the rebuild
   // does not read J, so it runs on the operator's side stream beside the x and
   // y stages and is joined before the fused kernel
+  // (or it was started after the previous matvec's fused kernel: rb_pending)
+  vie_op* opm = const_cast<vie_op*>(op);
   bool pre = false;
+  const bool side = !stored && op->oct32 != nullptr && op->rb_stream != nullptr;
   if constexpr (sizeof(T) == 4) {
-    if (!stored && op->oct32 != nullptr && op->rb_stream != nullptr) {
+    if (side && !op->rb_pending) {
       VIE_CUDA(cudaEventRecord(op->rb_fork, s));
       VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
       VIE_TRY(launch_octant(op, 0, op->rb_stream));
       VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
-      pre = true;
     }
+    pre = side;
+    if (side) opm->rb_pending = false;
   }
   launch_line_fft<T>(st.s[0], s);
   launch_line_fft<T>(st.s[1], s);
@@ -186,6 +191,15 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s, pre));
   launch_line_fft<T>(st.s[2], s);
   launch_line_fft<T>(st.s[3], s);
+  if (pre && (mv_flags & MV_PREFETCH_REBUILD)) {
+    // rebuild the scratch for the next matvec beside whatever the caller does
+    // next (in the solve: the Gram-Schmidt kernels, which leave issue slots free)
+    VIE_CUDA(cudaEventRecord(op->rb_fork, s));
+    VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
+    VIE_TRY(launch_octant(op, 0, op->rb_stream));
+    VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
+    opm->rb_pending = true;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "matvec launch");
   return VIE_OK;
@@ -194,23 +208,23 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
-                cudaStream_t s, const double* rscale, long long rscale_stride) {
+                cudaStream_t s, const double* rscale, long long rscale_stride, int mv_flags) {
   if (workspace_bytes_for(op, B) > op->ws.bytes) {
     VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
   }
   return matvec_run<T>(op, op->ws.ptr, in, out, B, path, pro_flags, epi_flags, chi, addend, active,
-                       s, rscale, rscale_stride);
+                       s, rscale, rscale_stride, mv_flags);
 }
 
 template int matvec_run<float>(const vie_op*, void*, const float2*, float2*, int, int, int, int,
                                const float2*, const float2*, const int*, cudaStream_t,
-                               const double*, long long);
+                               const double*, long long, int);
 template LineStages<float> make_line_stages<float>(const vie_op*, void*, const float2*, float2*, int,
                                                    int, int, const float2*, const float2*,
                                                    const int*, const double*, long long);
 template int matvec_impl<float>(const vie_op*, const float2*, float2*, int, int, int, int,
                                 const float2*, const float2*, const int*, cudaStream_t,
-                                const double*, long long);
+                                const double*, long long, int);
 template int matvec_impl<double>(const vie_op*, const double2*, double2*, int, int, int, int,
                                  const double2*, const double2*, const int*, cudaStream_t,
-                                 const double*, long long);
+                                 const double*, long long, int);

@@ -847,13 +847,14 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   const long long N = st->N;
   const float2* vk = st->V + (long long)k * B * N;
   float2* w = st->V + (long long)(k + 1) * B * N;
-  // w = A (sig_k Vraw_k)
+  // w = A (sig_k Vraw_k); the rebuild for the next matvec (the next step's or
+  // the cycle tail's) starts beside this step's Gram-Schmidt work
   if (!adjoint)
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s,
-                               st->sig + k, m + 1));
+                               st->sig + k, m + 1, MV_PREFETCH_REBUILD));
   else
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi, vk,
-                               st->active, s, st->sig + k, m + 1));
+                               st->active, s, st->sig + k, m + 1, MV_PREFETCH_REBUILD));
   VIE_TRY(join_givens(st, s));
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
   for (int pass = 0; pass < passes; ++pass) {
@@ -930,6 +931,7 @@ static int cycle_tail(const vie_op* op, SolverState* st, const float2* chi, int 
 static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int path, int adjoint,
                      int passes, bool use_graph, cudaStream_t s) {
   st->givens_pending = false;                 // every cycle ends joined
+  const_cast<vie_op*>(op)->rb_pending = false;   // (both side streams)
   if (!use_graph) {
     for (int k = 0; k < st->m; ++k) VIE_TRY(arnoldi_step(op, st, chi, k, path, adjoint, passes, s));
     return cycle_tail(op, st, chi, path, adjoint, s);

@@ -197,6 +197,9 @@ struct vie_op {
   // beside the x and y stages and is joined before the fused kernel
   cudaStream_t rb_stream = nullptr;
   cudaEvent_t rb_fork = nullptr, rb_join = nullptr;
+  // host-side, in launch order: chunk 0 of the next matvec's rebuild is already
+  // enqueued on rb_stream (started by the previous matvec, see MV_PREFETCH_REBUILD)
+  bool rb_pending = false;
   // stored spectra (optional)
   float2* spec32 = nullptr;  double2* spec64 = nullptr;
   FftPlan plan[3];
@@ -243,10 +246,15 @@ void component_axes(int c, int* a, int* b);
 double wavenumber(double freq_hz);
 
 // matvec internals (matvec.cu)
+// matvec_impl / matvec_run option: after the fused kernel, start rebuilding the
+// half fibres for the next FP32 Tucker matvec on the operator's side stream (the
+// next matvec joins it); the caller must make another Tucker matvec follow
+enum { MV_PREFETCH_REBUILD = 1 };
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
-                cudaStream_t s, const double* rscale = nullptr, long long rscale_stride = 0);
+                cudaStream_t s, const double* rscale = nullptr, long long rscale_stride = 0,
+                int mv_flags = 0);
 int ensure_workspace(vie_op* op, int B);
 // The four line-stage launches of one matvec (x, y, inverse y, inverse x).
 template <typename T> struct LineStages {
@@ -262,7 +270,7 @@ template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
                const int* active, cudaStream_t s, const double* rscale = nullptr,
-               long long rscale_stride = 0);
+               long long rscale_stride = 0, int mv_flags = 0);
 size_t workspace_bytes_for(const vie_op* op, int B);
 
 template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
