@@ -46,7 +46,85 @@ def parse():
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
+    p.add_argument("--record-traffic", metavar="NCU_CSV",
+                   help="turn an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum per launch "
+                        "into the row of --family in profiles/roofline_traffic.md, then exit")
+    p.add_argument("--family", help="kernel family of --record-traffic (e.g. fused_tucker)")
+    p.add_argument("--capture", default="", help="--record-traffic: the ncu command, for the record")
     return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# DRAM traffic of the roofline kernel, from ncu captures (profiles/roofline_traffic.md).
+# A row is used only while the library sources are unchanged since its capture.
+# ---------------------------------------------------------------------------
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+TRAFFIC_HEADER = ("| family | kernel | sources | launches | dram bytes per launch | workload | capture |\n"
+                  "|---|---|---|---|---|---|---|\n")
+
+
+def sources_digest():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1811_00484_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    [os.path.join(ROOT, "include", "vie.h")]):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_rows():
+    rows = {}
+    if os.path.exists(TRAFFIC_FILE):
+        for line in open(TRAFFIC_FILE):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) == 7 and cells[0] not in ("family", "---"):
+                rows[cells[0]] = cells
+    return rows
+
+
+def recorded_traffic(family):
+    r = traffic_rows().get(family)
+    if r is None or r[2] != sources_digest():
+        return None
+    return float(r[4])
+
+
+def record_traffic(args):
+    import csv
+    rows = list(csv.reader(open(args.record_traffic)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, mi, vi, ui = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    idx = hdr.index("ID")
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    names = set()
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        per[r[idx]] = per.get(r[idx], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
+        names.add(r[ki].split("(")[0].replace("void ", "").strip())
+    if not per:
+        raise SystemExit("no dram__bytes rows in " + args.record_traffic)
+    table = traffic_rows()
+    table[args.family] = [args.family, " ".join(sorted(names)), sources_digest(), str(len(per)),
+                          f"{sum(per.values()) / len(per):.0f}", "64^3 solve, every launch of one solve",
+                          args.capture.replace("|", "/")]
+    with open(TRAFFIC_FILE, "w") as fh:
+        fh.write("# DRAM traffic of the roofline kernel families\n\n"
+                 "Written by `bench.py --record-traffic` from ncu captures of `dram__bytes_read.sum` + "
+                 "`dram__bytes_write.sum` (one pass per launch) over every launch of one bench solve. "
+                 "`sources` is a digest of the library sources at capture time: `bench.py` reports a "
+                 "row's traffic only while the sources still match it, and null otherwise.\n\n")
+        fh.write(TRAFFIC_HEADER)
+        for k in sorted(table):
+            fh.write("| " + " | ".join(table[k]) + " |\n")
+    print(json.dumps({"family": args.family, "launches": len(per),
+                      "dram_bytes_per_launch": sum(per.values()) / len(per)}))
 
 
 def dist_env():
@@ -228,6 +306,8 @@ def run_matvec_mode(args):
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "matvec":
@@ -292,7 +372,13 @@ def main():
         t_tucker, mv_tucker, it_tucker = timed_solves("tucker", args.steps)
         kern_live = vie.profile_stop()
     clocks = clk.summary()
+    # the uncompressed solves carry the same instrumentation (the matching family)
+    dom_unc = {"fused_tucker": "fused_stored", "tucker_rebuild": None}.get(dom, dom)
+    if dom_unc:
+        vie.profile_start([dom_unc])
     t_unc, mv_unc, it_unc = timed_solves("uncompressed", args.steps)
+    if dom_unc:
+        vie.profile_stop()
 
     # end to end: host buffers in, host solution out, through the same C-ABI solve
     barrier()
@@ -383,8 +469,10 @@ def main():
                    "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in kern.values())), 4),
                    "GBps": round(gbs(v), 1)} for k, v in kern.items()}
     d = kern_live[dom]
+    traffic = recorded_traffic(dom)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(gbs(d), 1), "peak": peak,
-                "unit": "GB/s", "frac": round(gbs(d) / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(gbs(d) / peak, 4),
+                "traffic": round(traffic) if traffic is not None else None,
                 "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                 "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
