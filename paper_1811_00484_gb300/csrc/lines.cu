@@ -106,6 +106,36 @@ __global__ void __launch_bounds__(128, line_reg_min_blocks(R)) line_reg_kernel(c
   line_reg_group<R, HALF>(a, cg * kRegCols, o, bb, vec != 0, lane);
 }
 
+// Four-step variant (see line_fs_group) for N = 8 V with V = 4 R, R even.
+__host__ __device__ constexpr int line_fs_min_blocks(int V) { return V <= 16 ? 6 : 4; }
+
+template <int V, bool HALF>
+__global__ void __launch_bounds__(128, line_fs_min_blocks(V)) line_fs_kernel(const LineArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* xs = reinterpret_cast<float2*>(smem_raw) + (size_t)warp * kRegCols * fs_col_stride(V);
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int ncg = (a.ncol + kRegCols - 1) / kRegCols;
+  if (w >= (long long)ncg * a.nother * a.nbatch) return;        // warp-uniform; no barriers
+  const int cg = (int)(w % ncg);
+  const int o = (int)((w / ncg) % a.nother);
+  const int bb = (int)(w / ((long long)ncg * a.nother));
+  line_fs_group<V, HALF>(a, cg * kRegCols, o, bb, lane, xs);
+}
+
+template <int V>
+static void launch_fs_v(LineArgs<float> a, cudaStream_t s) {
+  const int ncg = (a.ncol + kRegCols - 1) / kRegCols;
+  const long long warps = (long long)ncg * a.nother * a.nbatch;
+  const int threads = a.threads > 0 && a.threads <= 128 ? a.threads : 128;
+  const unsigned grid = (unsigned)((warps + threads / 32 - 1) / (threads / 32));
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
+  const bool half = a.inverse ? (2 * a.lout == a.plan.N) : (2 * a.lin == a.plan.N);
+  launch_pdl(half ? line_fs_kernel<V, true> : line_fs_kernel<V, false>, dim3(grid), dim3(threads),
+             line_fs_smem(V, threads / 32), s, a);
+}
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 template <int R>
@@ -146,11 +176,11 @@ static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
   if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
   switch (N / 32) {
     case 1: launch_reg_r<1>(a, s); return true;
-    case 2: launch_reg_r<2>(a, s); return true;
+    case 2: launch_fs_v<8>(a, s); return true;
     case 3: launch_reg_r<3>(a, s); return true;
-    case 4: launch_reg_r<4>(a, s); return true;
+    case 4: launch_fs_v<16>(a, s); return true;
     case 5: launch_reg_r<5>(a, s); return true;
-    case 6: launch_reg_r<6>(a, s); return true;
+    case 6: launch_fs_v<24>(a, s); return true;
     case 8: launch_warp_r<8>(a, s); return true;
     case 10: launch_warp_r<10>(a, s); return true;
     case 12: launch_warp_r<12>(a, s); return true;

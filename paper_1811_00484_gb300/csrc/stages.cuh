@@ -311,6 +311,105 @@ __device__ __forceinline__ void line_reg_group(const LineArgs<float>& a, int c0,
   }
 }
 
+// Two-pass (four-step) variant for N = 8 V, V a multiple of 8: a warp owns
+// kRegCols adjacent columns and eight lanes per column, lane = 4 j + c.
+//   pass 1 (registers): lane (j, c) holds x[j + 8 m], m < V, of column c, takes
+//          the length-V DFT over m and multiplies by w_N^{j k1};
+//   exchange (shared memory, one write and one read per value);
+//   pass 2 (registers): for k1 = j + 8 t, the length-8 DFT over j gives
+//          X[k1 + V k2], k2 < 8.
+// The inverse runs the same steps with conjugate roots (unscaled).  For a
+// fixed register index the warp's 32 lanes touch 8 rows x 4 columns, i.e.
+// whole 32-byte sectors.  No shuffles.  HALF: forward from x[n < N/2] (m < V/2
+// nonzero), or inverse cropped to n < N/2 (k2 < 4).
+// Exchange layout per warp: [c][j][k1], row stride V+1, column stride
+// 8(V+1)+4 (both passes conflict-free within each half-warp).
+__host__ __device__ constexpr int fs_col_stride(int V) { return 8 * (V + 1) + 4; }
+__host__ __device__ constexpr size_t line_fs_smem(int V, int warps) {
+  return (size_t)warps * kRegCols * fs_col_stride(V) * sizeof(float2);
+}
+
+template <int V, bool HALF>
+__device__ __forceinline__ void line_fs_group(const LineArgs<float>& a, int c0, int o, int bb,
+                                              int lane, float2* xs) {
+  using C = float2;
+  constexpr int N = 8 * V;
+  constexpr int S = fs_col_stride(V);
+  const int j = lane >> 2, c = lane & 3;
+  C* xc = xs + c * S;
+  pdl_trigger();
+  pdl_wait();
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // warp-uniform
+  if (a.prof != nullptr && c0 == 0 && o == 0 && lane == 0) atomicAdd(a.prof, a.prof_batch_bytes);
+  const bool col_ok = c0 + c < a.ncol;
+  const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                       ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                       : 1.f;
+  const C* in = a.in + bb * a.in_bs + o * a.in_os + (long long)(c0 + c);
+  C* out = a.out + bb * a.out_bs + o * a.out_os + (long long)(c0 + c);
+  const bool inv = a.inverse != 0;
+  C v[V];
+  // pass 1: rows j + 8 m
+  constexpr int M1 = HALF ? V / 2 : V;         // forward: rows loaded (the rest is padding)
+#pragma unroll
+  for (int m = 0; m < V; ++m) {
+    const int p = j + 8 * m;
+    C x = make_float2(0.f, 0.f);
+    if ((inv || m < M1) && col_ok && p < a.lin) {
+      x = in[(long long)p * a.in_ls];
+      if (!inv) {
+        if (a.flags & PRO_RSCALE) x = rs * x;
+        if (a.flags & PRO_CONJ) x = conjg(x);
+        if (a.flags & PRO_CHI) x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + c)] * x;
+      }
+    }
+    v[m] = x;
+  }
+  if (!inv) {
+#pragma unroll
+    for (int m = M1; m < V; ++m) v[m] = make_float2(0.f, 0.f);   // zero padding, compile-time
+  }
+  reg_dft<C, float, V>(v, a.roots, N, inv);
+#pragma unroll
+  for (int k1 = 1; k1 < V; ++k1) {
+    const C w = a.roots[j * k1];
+    v[k1] = v[k1] * (inv ? conjg(w) : w);
+  }
+  // exchange: [c][j][k1]
+#pragma unroll
+  for (int k1 = 0; k1 < V; ++k1) xc[j * (V + 1) + k1] = v[k1];
+  __syncwarp();
+  // pass 2: k1 = j + 8 t, DFT over the eight j
+  constexpr int K2 = (HALF ? 4 : 8);           // inverse: outputs kept (cropped to N/2)
+#pragma unroll
+  for (int t = 0; t < V / 8; ++t) {
+    const int k1 = j + 8 * t;
+    C u[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + k1];
+    reg_dft<C, float, 8>(u, a.roots, N, inv);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      if (inv && k2 >= K2) continue;
+      const int p = k1 + V * k2;
+      if (!col_ok || p >= a.lout) continue;
+      C x = u[k2];
+      if (inv) {
+        x = a.scale * x;
+        if (a.flags & EPI_CONJ) x = conjg(x);
+        if (a.flags & (EPI_SUB | EPI_ADD)) {
+          if (a.flags & EPI_CHI)
+            x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + c)] * x;
+          C w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + c) + (long long)p * a.out_ls];
+          if (a.flags & EPI_RSCALE) w = rs * w;
+          x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+        }
+      }
+      out[(long long)p * a.out_ls] = x;
+    }
+  }
+}
+
 // Slot of z-frequency k in a row of the rebuilt half fibre: one padding slot
 // every 8 entries, so the lanes' folded, bit-reversed frequencies (stride R)
 // fall in different banks (at most 2-way for the radices used, 4-way at R=10).

@@ -87,6 +87,8 @@ template <typename C, typename T> struct RegDft<C, T, 6> : RegDftSplit<C, T, 2, 
 template <typename C, typename T> struct RegDft<C, T, 10> : RegDftSplit<C, T, 2, 5> {};
 template <typename C, typename T> struct RegDft<C, T, 12> : RegDftSplit<C, T, 4, 3> {};
 template <typename C, typename T> struct RegDft<C, T, 16> : RegDftSplit<C, T, 4, 4> {};
+template <typename C, typename T> struct RegDft<C, T, 24> : RegDftSplit<C, T, 3, 8> {};
+template <typename C, typename T> struct RegDft<C, T, 32> : RegDftSplit<C, T, 4, 8> {};
 
 // Per-lane constants of the lane transforms, computed once per kernel:
 //   tw[k1]  = w_N^{lane k1}                       (twiddle between the stages)
