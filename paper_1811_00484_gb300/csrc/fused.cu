@@ -224,6 +224,15 @@ __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
   }
 }
 
+// Four-step variant (fused_fs_group) for P3 = 8 V, V = 4 R with R even.
+__host__ __device__ constexpr int fused_fs_min_blocks(int V) { return V <= 8 ? 8 : (V <= 16 ? 5 : 4); }
+
+template <int V, bool STORED>
+__global__ void __launch_bounds__(96, fused_fs_min_blocks(V)) fused_fs_kernel(const FusedArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fused_fs_group<V, STORED>(a, a.g0 + blockIdx.x, reinterpret_cast<float2*>(smem_raw));
+}
+
 template <int R, bool STORED>
 static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   const size_t smem = fused_warp_smem(R, a.H3, a.r2max, a.r3max);
@@ -231,9 +240,20 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   a.prof = prof_bytes(fam);
   a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);
   a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(float2) : 0ull;
+  // the four-step kernel when R is even (and, on the Tucker path, the half
+  // fibres come from the rebuild scratch)
+  constexpr bool kFs = (R == 2 || R == 4 || R == 6);
+  const bool fs = kFs && (STORED || a.octant != nullptr);
+  const size_t fs_smem = fused_fs_smem(4 * R, a.H3);
   if (STORED || a.octant == nullptr) {
     ProfScope ps(fam, s);
     a.g0 = 0;
+    if constexpr (kFs) {
+      if (fs) {
+        launch_pdl(fused_fs_kernel<4 * R, STORED>, dim3(a.H1 * a.H2), dim3(96), fs_smem, s, a);
+        return;
+      }
+    }
     launch_pdl(fused_warp_kernel<R, STORED>, dim3(a.H1 * a.H2), dim3(128), smem, s, a);
     return;
   }
@@ -258,7 +278,14 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
     a.oct_k1a = k1a;
     a.g0 = k1a * a.H2;
     ProfScope ps(fam, s);
-    launch_pdl(fused_warp_kernel<R, STORED>, dim3(nk1 * a.H2), dim3(128), smem, s, a);
+    bool done = false;
+    if constexpr (kFs) {
+      if (fs) {
+        launch_pdl(fused_fs_kernel<4 * R, STORED>, dim3(nk1 * a.H2), dim3(96), fs_smem, s, a);
+        done = true;
+      }
+    }
+    if (!done) launch_pdl(fused_warp_kernel<R, STORED>, dim3(nk1 * a.H2), dim3(128), smem, s, a);
   }
 }
 
@@ -430,6 +457,12 @@ int fused_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_z_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<24, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<24, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   // octant_kernel also holds the six metadata records in static shared memory
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");

@@ -571,4 +571,148 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
   }
 }
 
+// Fused z stage with the four-step transform (P3 = 8 V): one CTA of three warps
+// per (k1, k2) mirror group, warp = Cartesian component of J and Y, lane =
+// 4 j + l with l the mirror line (up to four) and j the eighth of the line.
+//   forward: pass 1 / exchange / pass 2 as in line_fs_group, then the
+//            component's spectrum goes to a shared buffer spec[comp][l][f];
+//   product: each lane forms Y_comp[l][f] = s_comp sum_b G_comp,b[fold f] s_b J_b[l][f]
+//            (D G D, with G the rebuilt half fibre, or the stored spectra) for
+//            the frequencies f = j + 8 m its inverse pass 1 needs;
+//   inverse: pass 1 / exchange / pass 2 cropped to n3 outputs, written in place.
+// Every thread must call it.
+__host__ __device__ constexpr int fused_fs_spec_stride(int V) { return 8 * V + 4; }
+__host__ __device__ constexpr size_t fused_fs_smem(int V, int H3) {
+  return (size_t)(6 * ((H3 - 1) + ((H3 - 1) >> 3) + 1) + 3 * 4 * fused_fs_spec_stride(V) +
+                  3 * kRegCols * fs_col_stride(V)) *
+         sizeof(float2);
+}
+
+template <int V, bool STORED>
+__device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g, float2* smem) {
+  using C = float2;
+  constexpr int N = 8 * V;                     // P3
+  constexpr int XS = fs_col_stride(V);
+  constexpr int SS = fused_fs_spec_stride(V);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, comp = tid >> 5;  // three warps
+  const int j = lane >> 2, ln = lane & 3;
+  const int n3 = a.n3, H3 = a.H3;
+  const int k1 = g / a.H2, k2 = g % a.H2;
+  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
+  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
+  const bool valid = ln < nx * ny;
+  const int ix = valid ? ln / ny : 0, iy = valid ? ln % ny : 0;
+  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
+  const long long line_off = ((long long)kx * a.P2 + ky) * n3;
+  const int GS = ghalf_slot(H3 - 1) + 1;
+  C* ghalf = smem;                              // [6][GS]
+  C* spec = ghalf + 6 * GS;                     // [3][4][SS]
+  C* xw = spec + 3 * 4 * SS + comp * kRegCols * XS;   // this warp's exchange buffer
+  C* xc = xw + ln * XS;
+  pdl_trigger();
+  pdl_wait();
+  if (a.prof != nullptr && g == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
+  if (!STORED) {
+    // the group's half fibres, rebuilt for this matvec by octant_kernel
+    const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
+    for (int it = tid; it < 6 * H3; it += nth) {
+      const int c = it / H3, kk = it - c * H3;
+      ghalf[c * GS + ghalf_slot(kk)] = src[it];
+    }
+  }
+  // rows of G used by this warp's component: x: xx xy xz, y: xy yy yz, z: xz yz zz
+  const int g0 = comp == 0 ? 0 : (comp == 1 ? 1 : 2);
+  const int g1 = comp == 0 ? 1 : (comp == 1 ? 3 : 4);
+  const int g2 = comp == 0 ? 2 : (comp == 1 ? 4 : 5);
+  const float sx = ix ? -1.f : 1.f, sy = iy ? -1.f : 1.f;
+  const float sc = comp == 0 ? sx : (comp == 1 ? sy : 1.f);
+  __syncthreads();
+  for (int b = 0; b < a.B; ++b) {
+    if (a.active != nullptr && a.active[b] == 0) continue;   // block-uniform
+    C* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+    // forward pass 1: x[j + 8 m], m < V/2 (the rest is zero padding)
+    C v[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+      const int p = j + 8 * m;
+      v[m] = (m < V / 2 && valid && p < n3) ? line[p] : make_float2(0.f, 0.f);
+    }
+    reg_dft<C, float, V>(v, a.roots, N, false);
+#pragma unroll
+    for (int q = 1; q < V; ++q) v[q] = v[q] * a.roots[j * q];
+#pragma unroll
+    for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
+    __syncwarp();
+    // forward pass 2 -> spec[comp][ln][q + V k2]
+    C* sp = spec + (comp * 4 + ln) * SS;
+#pragma unroll
+    for (int t = 0; t < V / 8; ++t) {
+      const int q = j + 8 * t;
+      C u[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
+      reg_dft<C, float, 8>(u, a.roots, N, false);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sp[q + V * k] = u[k];
+    }
+    __syncthreads();
+    // product at f = j + 8 m, straight into the inverse pass 1 registers
+    const C* s0 = spec + (0 * 4 + ln) * SS;
+    const C* s1 = spec + (1 * 4 + ln) * SS;
+    const C* s2 = spec + (2 * 4 + ln) * SS;
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+      const int f = j + 8 * m;
+      C G0, G1, G2;
+      float sz = 1.f;
+      if (STORED) {
+        const long long off = ((long long)kx * a.P2 + ky) * N + f;
+        G0 = a.spec[g0 * a.spec_stride + off];
+        G1 = a.spec[g1 * a.spec_stride + off];
+        G2 = a.spec[g2 * a.spec_stride + off];
+      } else {
+        const bool zm = 2 * f > N;
+        const int fold = zm ? N - f : f;
+        sz = zm ? -1.f : 1.f;
+        const C* gp = ghalf + ghalf_slot(fold);
+        G0 = gp[g0 * GS];
+        G1 = gp[g1 * GS];
+        G2 = gp[g2 * GS];
+      }
+      // stored spectra are complete: no mirror signs
+      const float ex = STORED ? 1.f : sx, ey = STORED ? 1.f : sy;
+      C y = G0 * (ex * s0[f]) + G1 * (ey * s1[f]) + G2 * (sz * s2[f]);
+      if (!STORED) y = (comp == 2 ? sz : sc) * y;
+      v[m] = y;
+    }
+    // inverse pass 1 (exchange buffer free: pass 2 read it before the barrier)
+    reg_dft<C, float, V>(v, a.roots, N, true);
+#pragma unroll
+    for (int q = 1; q < V; ++q) v[q] = v[q] * conjg(a.roots[j * q]);
+#pragma unroll
+    for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
+    __syncwarp();
+    // inverse pass 2, cropped: n = q + V k2 < N / 2
+#pragma unroll
+    for (int t = 0; t < V / 8; ++t) {
+      const int q = j + 8 * t;
+      C u[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
+      reg_dft<C, float, 8>(u, a.roots, N, true);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int n = q + V * k;
+        if (valid && n < n3) line[n] = u[k];
+      }
+    }
+    __syncthreads();                           // spec and xw reused by the next right-hand side
+  }
+}
+
 }  // namespace vie
