@@ -169,7 +169,10 @@ __global__ void __launch_bounds__(128, fused_min_blocks(R)) fused_warp_kernel(co
 // kOctK2 independent multiply-adds; U3 is read transposed (consecutive k3 at
 // consecutive addresses) and the output rows (k3 fastest) are written
 // contiguously.
-constexpr int kOctK2 = 8;
+constexpr int kOctK2 = kOctantK2;
+__host__ __device__ constexpr size_t octant_smem(int r2max, int r3max) {
+  return octant_smem_bytes(r2max, r3max);
+}
 
 struct OctArgs {
   const CompMeta<float>* meta;
@@ -181,6 +184,8 @@ struct OctArgs {
 __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* W = reinterpret_cast<float2*>(smem_raw);     // [6][r3max][kOctK2]
+  float2* Ss = W + 6 * a.r3max * kOctK2;               // [6][r2max][r3max]  slab cores of k1
+  float2* U2s = Ss + 6 * a.r2max * a.r3max;            // [6][kOctK2][r2max] U2 rows k2_0 ..
   __shared__ CompMeta<float> meta[6];
   if (threadIdx.x < 6) meta[threadIdx.x] = a.meta[threadIdx.x];
   __syncthreads();
@@ -188,39 +193,68 @@ __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
   const int k2_0 = blockIdx.x * kOctK2;
   const int nk2 = min(kOctK2, a.H2 - k2_0);
   const int r23 = a.r2max * a.r3max;
-  // W[c][q][t] = sum_b U2_c[k2_0 + t, b] S_c[k1][b, q]: one (c, q, t) per thread,
-  // t fastest (conflict-free stores)
-  for (int it = threadIdx.x; it < 6 * a.r3max * kOctK2; it += blockDim.x) {
-    const int t = it % kOctK2, cq = it / kOctK2;
-    const int c = cq / a.r3max, q = cq - c * a.r3max;
+  // stage the slab cores of k1 and the U2 rows of this CTA's k2 (all loads in flight)
+  for (int it = threadIdx.x; it < 6 * r23; it += blockDim.x) {
+    const int c = it / r23;
+    Ss[it] = meta[c].slab[(long long)k1 * r23 + (it - c * r23)];
+  }
+  for (int it = threadIdx.x; it < 6 * kOctK2 * a.r2max; it += blockDim.x) {
+    const int b = it % a.r2max, ct = it / a.r2max, t = ct % kOctK2, c = ct / kOctK2;
     const CompMeta<float>& m = meta[c];
-    float2 acc = make_float2(0.f, 0.f);
-    if (q < m.r3 && t < nk2) {
-      const float2* S = m.slab + (long long)k1 * r23 + q;
-      const float2* u2 = m.U2 + (long long)(k2_0 + t) * m.r2;
-#pragma unroll 4
-      for (int b = 0; b < m.r2; ++b) acc = cmadd(u2[b], S[b * a.r3max], acc);
-    }
-    W[it] = acc;
+    U2s[it] = (t < nk2 && b < m.r2) ? m.U2[(long long)(k2_0 + t) * m.r2 + b] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float2* out = a.out + ((long long)k1l * a.H2 + k2_0) * 6 * a.H3;
-  for (int it = threadIdx.x; it < 6 * a.H3; it += blockDim.x) {
-    const int c = it / a.H3, kk = it - c * a.H3;
-    const CompMeta<float>& m = meta[c];
-    const float2* u3t = m.U3t + kk;           // U3_c[kk, q] at u3t[q * H3]
-    const float2* w = W + c * a.r3max * kOctK2;
+  // W[c][q][t] = sum_b U2_c[k2_0 + t, b] S_c[k1][b, q]: one (c, q) per thread, all t
+  for (int it = threadIdx.x; it < 6 * a.r3max; it += blockDim.x) {
+    const int c = it / a.r3max, q = it - c * a.r3max;
+    const int r2 = meta[c].r2;
+    const float2* S = Ss + c * r23 + q;
+    const float2* u2 = U2s + c * kOctK2 * a.r2max;
     float2 acc[kOctK2];
 #pragma unroll
     for (int t = 0; t < kOctK2; ++t) acc[t] = make_float2(0.f, 0.f);
-    for (int q = 0; q < m.r3; ++q) {
-      const float2 u = u3t[(long long)q * a.H3];
+    for (int b = 0; b < r2; ++b) {
+      const float2 sv = S[b * a.r3max];
 #pragma unroll
-      for (int t = 0; t < kOctK2; ++t) acc[t] = cmadd(w[q * kOctK2 + t], u, acc[t]);
+      for (int t = 0; t < kOctK2; ++t) acc[t] = cmadd(u2[t * a.r2max + b], sv, acc[t]);
     }
 #pragma unroll
-    for (int t = 0; t < kOctK2; ++t)
-      if (t < nk2) out[(long long)t * 6 * a.H3 + it] = acc[t];
+    for (int t = 0; t < kOctK2; ++t) W[it * kOctK2 + t] = acc[t];
+  }
+  __syncthreads();
+  // G_c[k1, k2_0 + t, kk] = sum_q W[c][q][t] U3_c[kk, q]: two kk per thread, all t
+  float2* out = a.out + ((long long)k1l * a.H2 + k2_0) * 6 * a.H3;
+  const int hk = (a.H3 + 1) / 2;                       // kk pairs per component
+  for (int it = threadIdx.x; it < 6 * hk; it += blockDim.x) {
+    const int c = it / hk, kp = it - c * hk;
+    const int kk0 = 2 * kp, kk1 = min(2 * kp + 1, a.H3 - 1);
+    const CompMeta<float>& m = meta[c];
+    const float2* u3t = m.U3t;                         // U3_c[kk, q] at u3t[q * H3 + kk]
+    const float4* w = reinterpret_cast<const float4*>(W + c * a.r3max * kOctK2);
+    float2 acc0[kOctK2], acc1[kOctK2];
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t) acc0[t] = acc1[t] = make_float2(0.f, 0.f);
+    for (int q = 0; q < m.r3; ++q) {
+      const float2 u0 = u3t[(long long)q * a.H3 + kk0];
+      const float2 u1 = u3t[(long long)q * a.H3 + kk1];
+#pragma unroll
+      for (int t2 = 0; t2 < kOctK2 / 2; ++t2) {
+        const float4 wv = w[q * (kOctK2 / 2) + t2];     // W[c][q][2 t2], W[c][q][2 t2 + 1]
+        const float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
+        acc0[2 * t2] = cmadd(wa, u0, acc0[2 * t2]);
+        acc1[2 * t2] = cmadd(wa, u1, acc1[2 * t2]);
+        acc0[2 * t2 + 1] = cmadd(wb, u0, acc0[2 * t2 + 1]);
+        acc1[2 * t2 + 1] = cmadd(wb, u1, acc1[2 * t2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kOctK2; ++t) {
+      if (t < nk2) {
+        float2* o = out + ((long long)t * 6 + c) * a.H3;
+        o[kk0] = acc0[t];
+        if (kk1 != kk0) o[kk1] = acc1[t];
+      }
+    }
   }
 }
 
@@ -267,7 +301,7 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   o.H2 = a.H2;
   o.H3 = a.H3;
   o.out = const_cast<float2*>(a.octant);
-  const size_t osmem = (size_t)kOctK2 * 6 * a.r3max * sizeof(float2);
+  const size_t osmem = octant_smem(a.r2max, a.r3max);
   for (int k1a = 0; k1a < a.H1; k1a += chunk) {
     const int nk1 = std::min(chunk, a.H1 - k1a);
     o.k1a = k1a;
@@ -422,7 +456,7 @@ int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
   o.k1a = k1a;
   o.out = op->oct32;
   const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
-  const size_t osmem = (size_t)vie::kOctK2 * 6 * o.r3max * sizeof(float2);
+  const size_t osmem = vie::octant_smem(o.r2max, o.r3max);
   ProfScope ps(PF_REBUILD, s);
   vie::octant_kernel<<<dim3((o.H2 + vie::kOctK2 - 1) / vie::kOctK2, nk1), 256, osmem, s>>>(o);
   cudaError_t e = cudaGetLastError();

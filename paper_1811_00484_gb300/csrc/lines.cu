@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128, line_reg_min_blocks(R)) line_reg_kernel(c
 }
 
 // Four-step variant (see line_fs_group) for N = 8 V with V = 4 R, R even.
-__host__ __device__ constexpr int line_fs_min_blocks(int V) { return V <= 16 ? 6 : 4; }
+__host__ __device__ constexpr int line_fs_min_blocks(int V) { return V <= 16 ? 8 : 4; }
 
 template <int V, bool HALF>
 __global__ void __launch_bounds__(128, line_fs_min_blocks(V)) line_fs_kernel(const LineArgs<float> a) {

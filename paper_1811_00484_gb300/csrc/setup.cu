@@ -611,7 +611,8 @@ static int finish_operator(vie_op* op) {
   VIE_TRY(launch_slab_cores<double>(op, 0));
   // FP32 scratch for the per-matvec rebuild of the half fibres (register-path
   // fused kernel): whole k1 planes of [H2][6][H3], as many as fit in kOctBudget
-  if (op->P[2] % 32 == 0 && vie::warp_fft_supported(op->P[2] / 32)) {
+  if (op->P[2] % 32 == 0 && vie::warp_fft_supported(op->P[2] / 32) &&
+      octant_smem_bytes(op->rmax[1], op->rmax[2]) <= kOctantSmemMax) {
     constexpr size_t kOctBudget = 64u << 20;
     const size_t plane = (size_t)op->H[1] * 6 * op->H[2] * sizeof(float2);
     op->oct_k1 = (int)std::max<size_t>(1, std::min<size_t>(op->H[0], kOctBudget / plane));

@@ -274,7 +274,15 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
 size_t workspace_bytes_for(const vie_op* op, int B);
 
 template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
-// rebuild of the half fibres of k1 in [k1a, k1a + oct_k1) into op->oct32 (fused.cu)
+// rebuild of the half fibres of k1 in [k1a, k1a + oct_k1) into op->oct32 (fused.cu);
+// its dynamic shared memory holds W [6][r3][8], the slab cores of k1 [6][r2][r3]
+// and eight U2 rows [6][8][r2]; operators whose ranks make that exceed
+// kOctantSmemMax keep the in-CTA rebuild instead
+constexpr int kOctantK2 = 8;
+constexpr size_t kOctantSmemMax = 200u << 10;
+__host__ __device__ constexpr size_t octant_smem_bytes(int r2max, int r3max) {
+  return (size_t)(6 * r3max * kOctantK2 + 6 * r2max * r3max + 6 * kOctantK2 * r2max) * sizeof(float2);
+}
 int launch_octant(const vie_op* op, int k1a, cudaStream_t s);
 
 // setup internals (setup.cu)
