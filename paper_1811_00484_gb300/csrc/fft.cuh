@@ -66,6 +66,51 @@ __device__ __forceinline__ void dft8(C* v, bool inv) {
   v[7] = e3 - t3;
 }
 
+// v * w16^e with w16 = exp(-/+ 2 pi i / 16), e in {1, 2, 3, 4, 6, 9} (compile time)
+template <typename C, typename T, int E>
+__device__ __forceinline__ C w16mul(C v, bool inv) {
+  const T c = (T)0.92387953251128675613, s = (T)0.38268343236508977173;   // cos, sin(pi/8)
+  const T r = (T)0.70710678118654752440;
+  T wr, wi;                                            // forward root
+  if (E == 1) { wr = c; wi = -s; }
+  else if (E == 2) { wr = r; wi = -r; }
+  else if (E == 3) { wr = s; wi = -c; }
+  else if (E == 4) { wr = 0; wi = -1; }
+  else if (E == 6) { wr = -r; wi = -r; }
+  else { wr = -c; wi = s; }                            // E == 9
+  if (inv) wi = -wi;
+  if (E == 4) return inv ? mul_i(v) : mul_mi(v);
+  return mk(v.x * wr - v.y * wi, v.x * wi + v.y * wr);
+}
+
+// length-16 DFT in registers, natural order in and out: 4 x 4 with in-place
+// radix-4 butterflies (n = 4 n1 + n2, k = k1 + 4 k2) and constant twiddles
+template <typename C, typename T>
+__device__ __forceinline__ void dft16(C* v, bool inv) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2], inv);
+  // v[4 k1 + n2] *= w16^{n2 k1}
+  v[5] = w16mul<C, T, 1>(v[5], inv);
+  v[6] = w16mul<C, T, 2>(v[6], inv);
+  v[7] = w16mul<C, T, 3>(v[7], inv);
+  v[9] = w16mul<C, T, 2>(v[9], inv);
+  v[10] = w16mul<C, T, 4>(v[10], inv);
+  v[11] = w16mul<C, T, 6>(v[11], inv);
+  v[13] = w16mul<C, T, 3>(v[13], inv);
+  v[14] = w16mul<C, T, 6>(v[14], inv);
+  v[15] = w16mul<C, T, 9>(v[15], inv);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3], inv);
+  // X[k1 + 4 k2] sits in v[4 k1 + k2]: transpose (a register permutation)
+  C t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <typename C, typename T>
 __device__ __forceinline__ void dft3(C* v, bool inv) {
   const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)

@@ -86,7 +86,9 @@ template <typename C, typename T, int R1, int R2> struct RegDftSplit {
 template <typename C, typename T> struct RegDft<C, T, 6> : RegDftSplit<C, T, 2, 3> {};
 template <typename C, typename T> struct RegDft<C, T, 10> : RegDftSplit<C, T, 2, 5> {};
 template <typename C, typename T> struct RegDft<C, T, 12> : RegDftSplit<C, T, 4, 3> {};
-template <typename C, typename T> struct RegDft<C, T, 16> : RegDftSplit<C, T, 4, 4> {};
+template <typename C, typename T> struct RegDft<C, T, 16> {
+  static __device__ __forceinline__ void run(C* v, const C*, int, bool inv) { dft16<C, T>(v, inv); }
+};
 template <typename C, typename T> struct RegDft<C, T, 24> : RegDftSplit<C, T, 3, 8> {};
 template <typename C, typename T> struct RegDft<C, T, 32> : RegDftSplit<C, T, 4, 8> {};
 
