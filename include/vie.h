@@ -272,6 +272,25 @@ int vie_solve(const vie_op* op, const void* chi, const void* rhs, void* w, int B
               vie_solve_info* info, void* stream);
 
 /*
+ * Several independent solves, e.g. the mixed-grid batch of 48^3, 64^3 and 80^3
+ * problems with their own right-hand sides (Section VI.C solve for each): the
+ * `count` solves run concurrently on the device, each as vie_solve would run
+ * it (its own internal stream and restart-cycle graphs, driven by its own host
+ * thread), so small grids fill the GPU together.  Results are those of `count`
+ * separate vie_solve calls.  ops, chi, rhs, w, B: host arrays of `count`
+ * entries, laid out as for vie_solve on the respective operator; the
+ * operators must be distinct.  flags, precision and opts apply to every
+ * solve; info: `count` records or NULL.  Ordered after the work already on
+ * `stream`, and the caller's stream waits for every solve.  Returns VIE_OK
+ * when every solve did, else the status of the first failing one (the others
+ * still complete).  The paper solves one problem at a time; this entry point
+ * has no counterpart there.
+ */
+int vie_solve_multi(const vie_op* const* ops, const void* const* chi, const void* const* rhs,
+                    void* const* w, const int* B, int count, int flags, int precision,
+                    const vie_solve_opts* opts, vie_solve_info* info, void* stream);
+
+/*
  * Contrast gradient from a forward field E and an adjoint solution lam:
  *   grad[v] = scale * sum_b sum_a lam[b,a,v] conj(E[b,a,v]).
  * For the misfit L = sum |E - E_target|^2 with A^H lam = G^H (E - E_target)

@@ -36,7 +36,8 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_reserve", "vie_matvec", "vie_matvec_adjoint", "vie_apply_system",
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
-           "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune")
+           "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune",
+           "vie_solve_multi")
 
 
 class VieError(RuntimeError):
@@ -95,6 +96,9 @@ def _load():
         "vie_matvec_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                              ctypes.POINTER(ci), ci, vp],
         "vie_autotune": [vp, ci, vp],
+        "vie_solve_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                            ctypes.POINTER(vp), ctypes.POINTER(ci), ci, ci, ci,
+                            ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
         "vie_apply_system": [vp, vp, vp, vp, ci, ci, ci, ci, vp],
         "vie_total_field": [vp, vp, vp, vp, ci, ci, ci, vp],
         "vie_solve": [vp, vp, vp, vp, ci, ci, ci, ctypes.POINTER(SolveOpts),
@@ -277,18 +281,13 @@ class Operator:
         if x0 is not None:
             w.copy_(x0)
             flags |= VIE_SOLVE_X0
-        if inner_tol is None:
-            inner_tol = max(tol, 1e-5) if refine else tol
-        opts = SolveOpts(float(tol), int(restart), int(max_outer), float(inner_tol),
-                         int(max_refine), PATHS[path], int(bool(use_graph)), int(bool(refine)),
-                         int(orth))
+        opts = _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph, refine,
+                           orth)
         inf = SolveInfo()
         st = lib.vie_solve(self._h, _dev(chi, "chi", self.n), _dev(rhs, "rhs", self.n),
                            _dev(w, "w", self.n), B, flags, _precision(rhs), ctypes.byref(opts),
                            ctypes.byref(inf), _stream())
-        info = {"converged": bool(inf.converged), "refine_steps": inf.refine_steps,
-                "iterations": inf.iterations, "matvecs": inf.matvecs, "relres": inf.relres,
-                "history": list(inf.history[:inf.refine_steps + 1]), "status": st}
+        info = _solve_info(inf, st)
         if st != VIE_OK and (raise_on_failure or st != 4):
             _check(st, "vie_solve")
         return w, info
@@ -319,6 +318,45 @@ class Operator:
 PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy", "line_ix",
                     "tucker_rebuild", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
                     "setup")
+
+
+def _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph, refine, orth):
+    if inner_tol is None:
+        inner_tol = max(tol, 1e-5) if refine else tol
+    return SolveOpts(float(tol), int(restart), int(max_outer), float(inner_tol), int(max_refine),
+                     PATHS[path], int(bool(use_graph)), int(bool(refine)), int(orth))
+
+
+def _solve_info(inf, st):
+    return {"converged": bool(inf.converged), "refine_steps": inf.refine_steps,
+            "iterations": inf.iterations, "matvecs": inf.matvecs, "relres": inf.relres,
+            "history": list(inf.history[:inf.refine_steps + 1]), "status": st}
+
+
+def solve_multi(ops, chis, rhss, incident=True, adjoint=False, tol=1e-6, restart=50, max_outer=200,
+                inner_tol=None, max_refine=20, path="tucker", use_graph=True, refine=True, orth=1):
+    """Independent solves on several operators (grids may differ), run concurrently
+    (vie_solve_multi).  Returns [(w, info)] in the order of ``ops``."""
+    torch = _torch()
+    count = len(ops)
+    if len(chis) != count or len(rhss) != count:
+        raise ValueError("one contrast and one right-hand side per operator")
+    dtypes = {r.dtype for r in rhss}
+    if len(dtypes) != 1:
+        raise TypeError("all right-hand sides must share one dtype")
+    ws = [torch.empty_like(r) for r in rhss]
+    flags = (VIE_SOLVE_ADJOINT if adjoint else 0) | (VIE_SOLVE_RHS_INCIDENT if incident else 0)
+    opts = _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph, refine, orth)
+    infs = (SolveInfo * count)()
+    hs = (ctypes.c_void_p * count)(*[op._h.value for op in ops])
+    cp = (ctypes.c_void_p * count)(*[_dev(c, "chi", op.n).value for op, c in zip(ops, chis)])
+    rp = (ctypes.c_void_p * count)(*[_dev(r, "rhs", op.n).value for op, r in zip(ops, rhss)])
+    wp = (ctypes.c_void_p * count)(*[_dev(w, "w", op.n).value for op, w in zip(ops, ws)])
+    bs = (ctypes.c_int * count)(*[_batch(r, op.n) for op, r in zip(ops, rhss)])
+    st = lib.vie_solve_multi(hs, cp, rp, wp, bs, count, flags, _precision(rhss[0]),
+                             ctypes.byref(opts), infs, _stream())
+    _check(st, "vie_solve_multi")
+    return [(w, _solve_info(infs[p], VIE_OK)) for p, w in enumerate(ws)]
 
 
 def matvec_multi(ops, Js, outs=None):

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "vie_internal.cuh"
@@ -299,6 +300,48 @@ int vie_solve(const vie_op* op, const void* chi, const void* rhs, void* w, int B
   vie_solve_info local;
   return solve_impl(op, chi, rhs, w, B, flags, precision, opts, info ? info : &local,
                     static_cast<cudaStream_t>(stream));
+}
+
+int vie_solve_multi(const vie_op* const* ops, const void* const* chi, const void* const* rhs,
+                    void* const* w, const int* B, int count, int flags, int precision,
+                    const vie_solve_opts* opts, vie_solve_info* info, void* stream) {
+  CLEAR_ERROR();
+  if (!ops || !chi || !rhs || !w || !B || count < 1 || !opts) {
+    set_error("NULL argument or empty problem list");
+    return VIE_ERR_ARG;
+  }
+  for (int p = 0; p < count; ++p) {
+    for (int q = 0; q < p; ++q)
+      if (ops[q] == ops[p]) {
+        set_error("problems %d and %d share an operator", q, p);
+        return VIE_ERR_ARG;
+      }
+  }
+  if (count == 1)
+    return vie_solve(ops[0], chi[0], rhs[0], w[0], B[0], flags, precision, opts,
+                     info ? &info[0] : nullptr, stream);
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  std::vector<int> status(count, VIE_OK);
+  std::vector<std::string> message(count);
+  std::vector<std::thread> threads;
+  threads.reserve(count);
+  for (int p = 0; p < count; ++p) {
+    threads.emplace_back([&, p]() {
+      cudaSetDevice(dev);
+      status[p] = vie_solve(ops[p], chi[p], rhs[p], w[p], B[p], flags, precision, opts,
+                            info ? &info[p] : nullptr, stream);
+      if (status[p] != VIE_OK) message[p] = vie_last_error();
+    });
+  }
+  for (std::thread& t : threads) t.join();
+  for (int p = 0; p < count; ++p) {
+    if (status[p] != VIE_OK) {
+      set_error("problem %d: %s", p, message[p].c_str());
+      return status[p];
+    }
+  }
+  return VIE_OK;
 }
 
 int vie_contrast_gradient(const vie_op* op, const void* lam, const void* E, void* grad, int B,

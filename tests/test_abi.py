@@ -58,6 +58,20 @@ def test_null_operator_is_rejected():
     vie.lib.vie_destroy(None)
 
 
+def test_solve_multi_rejects_bad_problem_lists():
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    opts = vie.SolveOpts(1e-6, 50, 200, 1e-5, 20, 0, 1, 1, 1)
+    P = ctypes.c_void_p * 2
+    fake = P(ctypes.c_void_p(16), ctypes.c_void_p(16))        # the same operator twice
+    bufs = P(ctypes.c_void_p(64), ctypes.c_void_p(128))
+    bs = (ctypes.c_int * 2)(1, 1)
+    lib = vie.lib
+    assert lib.vie_solve_multi(None, bufs, bufs, bufs, bs, 2, 0, 0, ctypes.byref(opts), None, None) == 1
+    assert lib.vie_solve_multi(fake, bufs, bufs, bufs, bs, 0, 0, 0, ctypes.byref(opts), None, None) == 1
+    assert lib.vie_solve_multi(fake, bufs, bufs, bufs, bs, 2, 0, 0, ctypes.byref(opts), None, None) == 1
+    assert "share an operator" in lib.vie_last_error().decode()
+
+
 def test_struct_layouts_match_header():
     """ctypes mirrors of the header structs have the C sizes."""
     vie = pytest.importorskip("paper_1811_00484_gb300")
