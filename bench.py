@@ -133,6 +133,21 @@ def record_traffic(args):
                       "dram_bytes_per_launch": sum(per.values()) / len(per)}))
 
 
+def reduce_ranks(t_local, count_local, world):
+    """Whole-job figures from the per-rank ones: the slowest rank's time (max) and the
+    operator applications of all ranks (sum).  One rank: unchanged."""
+    if world == 1:
+        return t_local, count_local
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(count_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -487,7 +502,11 @@ def main():
                "sample": f"{count} FP64 oracle system matvecs ({n[0]}^3, Tucker-rebuilt spectra) "
                          f"in {el:.1f} s"}
 
-    value = world * mv_tucker / t_tucker
+    # whole job: matvecs of every rank over the slowest rank's time
+    t_tucker, mv_all = reduce_ranks(t_tucker, mv_tucker, world)
+    t_unc, mv_unc_all = reduce_ranks(t_unc, mv_unc, world)
+    t_e2e, mv_e2e_all = reduce_ranks(t_e2e, mv_e2e, world)
+    value = mv_all / t_tucker
     peak, peak_kind = measured_peaks()
 
     def gbs(e):
@@ -525,7 +544,7 @@ def main():
                   "uncompressed_ms": 1e3 * t_unc / args.steps,
                   "iterations": it_tucker[-1]["iterations"], "refine_steps": it_tucker[-1]["refine_steps"],
                   "relres": it_tucker[-1]["relres"],
-                  "uncompressed_matvecs_per_s": world * mv_unc / t_unc},
+                  "uncompressed_matvecs_per_s": mv_unc_all / t_unc},
         "matvec": {"tucker_per_s": mv_rate_t, "tucker_ms": mv_ms_t,
                    "uncompressed_per_s": mv_rate_u, "uncompressed_ms": mv_ms_u,
                    "rel_err_vs_oracle": acc,
@@ -535,7 +554,7 @@ def main():
                    "rebuild_scratch_bytes": info["rebuild_scratch_bytes"], "ranks": info["ranks"]},
         "batched": batched,
         "clocks": clocks,
-        "e2e": {"value": world * mv_e2e / t_e2e, "unit": UNIT,
+        "e2e": {"value": mv_e2e_all / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": chi_h.numel() * 8 + einc_h.numel() * 8,
                 "d2h_bytes_per_step": w_h.numel() * 8},
         "cpu_baseline": cpu,
