@@ -157,6 +157,18 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
   return st;
 }
 
+// Rebuild the scratch for the next FP32 Tucker matvec on the side stream, ordered
+// after the work already on s (the fused kernel that last read the scratch).
+int prefetch_rebuild(const vie_op* op, cudaStream_t s) {
+  if (op->oct32 == nullptr || op->rb_stream == nullptr) return VIE_OK;
+  VIE_CUDA(cudaEventRecord(op->rb_fork, s));
+  VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
+  VIE_TRY(launch_octant(op, 0, op->rb_stream));
+  VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
+  const_cast<vie_op*>(op)->rb_pending = true;
+  return VIE_OK;
+}
+
 // The stages of one matvec with the caller-chosen scratch `ws` (T1 then T2).
 template <typename T>
 int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, int path,
@@ -191,15 +203,7 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s, pre));
   launch_line_fft<T>(st.s[2], s);
   launch_line_fft<T>(st.s[3], s);
-  if (pre && (mv_flags & MV_PREFETCH_REBUILD)) {
-    // rebuild the scratch for the next matvec beside whatever the caller does
-    // next (in the solve: the Gram-Schmidt kernels, which leave issue slots free)
-    VIE_CUDA(cudaEventRecord(op->rb_fork, s));
-    VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
-    VIE_TRY(launch_octant(op, 0, op->rb_stream));
-    VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
-    opm->rb_pending = true;
-  }
+  if (pre && (mv_flags & MV_PREFETCH_REBUILD)) VIE_TRY(prefetch_rebuild(op, s));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "matvec launch");
   return VIE_OK;

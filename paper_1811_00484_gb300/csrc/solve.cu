@@ -851,10 +851,10 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   // the cycle tail's) starts beside this step's Gram-Schmidt work
   if (!adjoint)
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s,
-                               st->sig + k, m + 1, MV_PREFETCH_REBUILD));
+                               st->sig + k, m + 1));
   else
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi, vk,
-                               st->active, s, st->sig + k, m + 1, MV_PREFETCH_REBUILD));
+                               st->active, s, st->sig + k, m + 1));
   VIE_TRY(join_givens(st, s));
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
   for (int pass = 0; pass < passes; ++pass) {
@@ -866,6 +866,8 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
                  (const float2*)st->V, (const float2*)w, k, B, N, G, m + 1, st->partial, mask,
                  prof_bytes(PF_DOTS), (k + 2) * vec);
     }
+    // the next matvec's rebuild, beside the rest of this step's Gram-Schmidt work
+    if (pass == 0 && path == VIE_PATH_TUCKER) VIE_TRY(prefetch_rebuild(op, s));
     {
       ProfScope ps(PF_SMALL, s);
       launch_pdl(reduce_dots_kernel, dim3(k + 1, B), dim3(kReduceThreads), 0, s,

@@ -250,6 +250,8 @@ double wavenumber(double freq_hz);
 // half fibres for the next FP32 Tucker matvec on the operator's side stream (the
 // next matvec joins it); the caller must make another Tucker matvec follow
 enum { MV_PREFETCH_REBUILD = 1 };
+// start that rebuild now (after the work already on s); the next matvec joins it
+int prefetch_rebuild(const vie_op* op, cudaStream_t s);
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
