@@ -78,7 +78,10 @@ enum {
     VIE_STORE_UNCOMPRESSED = 1,  /* also keep the six full spectra (the paper's
                                     "traditional FFT-JVIE", Table II row 1) in
                                     c64 and c128, for VIE_PATH_UNCOMPRESSED     */
-    VIE_SELF_TERM_PV = 2         /* self term without the -1/3 depolarisation  */
+    VIE_SELF_TERM_PV = 2,        /* self term without the -1/3 depolarisation  */
+    VIE_REBUILD_SIMT = 4         /* rebuild the half fibres of eq. (13) with
+                                    FP32 CUDA-core FMAs instead of the tensor
+                                    cores (3xTF32 mma); for comparison          */
 };
 
 /* vie_solve flags */
@@ -117,6 +120,10 @@ typedef struct vie_op_info_t {
     int line_threads[4];         /* CTA size of the x, y, inverse y, inverse x
                                     FFT stages (vie_autotune's choice)          */
     int tuned_batch;             /* batch vie_autotune timed at (0 = defaults)  */
+    int rebuild_kernel;          /* how each FP32 Tucker matvec rebuilds the
+                                    half fibres: 0 inside the fused z-stage
+                                    CTAs (no scratch), 1 FP32 FMAs into the
+                                    scratch, 2 tensor cores (3xTF32) into it    */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */

@@ -27,7 +27,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 VIE_C64, VIE_C128 = 0, 1
 PATHS = {"tucker": 0, "uncompressed": 1}
 RANK_RULES = {"tail": 0, "sigma_max": 1}
-VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV = 1, 2
+VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT = 1, 2, 4
+REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "tensor_cores"}
 VIE_SOLVE_ADJOINT, VIE_SOLVE_RHS_INCIDENT, VIE_SOLVE_X0 = 1, 2, 4
 COMPONENTS = ("xx", "xy", "xz", "yy", "yz", "zz")
 
@@ -57,7 +58,8 @@ class OpInfo(ctypes.Structure):
                 ("slab_bytes", ctypes.c_size_t), ("rebuild_scratch_bytes", ctypes.c_size_t),
                 ("uncompressed_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("has_uncompressed", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int)]
+                ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int),
+                ("rebuild_kernel", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -172,14 +174,17 @@ class Operator:
     """The compressed J-block operator of a uniform grid (vie_tucker_compress)."""
 
     def __init__(self, n, h, freq_hz, tol, rank_rule="tail", store_uncompressed=False,
-                 self_term="full"):
+                 self_term="full", rebuild="tensor_cores"):
+        if rebuild not in ("tensor_cores", "simt"):
+            raise ValueError("rebuild must be 'tensor_cores' or 'simt'")
         if isinstance(n, int):
             n = (n, n, n)
         self.n = tuple(int(v) for v in n)
         self.h, self.freq_hz, self.tol = float(h), float(freq_hz), float(tol)
         self._grid = Grid(self.n[0], self.n[1], self.n[2], self.h, self.freq_hz)
         flags = (VIE_STORE_UNCOMPRESSED if store_uncompressed else 0) | \
-                (VIE_SELF_TERM_PV if self_term == "pv" else 0)
+                (VIE_SELF_TERM_PV if self_term == "pv" else 0) | \
+                (VIE_REBUILD_SIMT if rebuild == "simt" else 0)
         handle = ctypes.c_void_p()
         _check(lib.vie_tucker_compress(ctypes.byref(self._grid), self.tol, RANK_RULES[rank_rule],
                                        flags, _stream(), ctypes.byref(handle)),
@@ -209,7 +214,8 @@ class Operator:
                 "uncompressed_bytes": inf.uncompressed_bytes,
                 "workspace_bytes": inf.workspace_bytes,
                 "has_uncompressed": bool(inf.has_uncompressed), "max_batch": inf.max_batch,
-                "line_threads": tuple(inf.line_threads), "tuned_batch": inf.tuned_batch}
+                "line_threads": tuple(inf.line_threads), "tuned_batch": inf.tuned_batch,
+                "rebuild_kernel": REBUILD_KERNELS[inf.rebuild_kernel]}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""

@@ -42,16 +42,22 @@ int component_parity(int c, int axis) {
   return ((a == axis) + (b == axis)) % 2 ? -1 : 1;
 }
 
-int persistent_grid(const void* kernel, int threads, size_t smem, long long work) {
+int device_sms() {
   static int sms = 0;
   if (sms == 0) {
-    int dev = 0;
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
       cudaGetLastError();
-      sms = 152;
+      v = 152;
     }
+    sms = v;
   }
+  return sms;
+}
+
+int persistent_grid(const void* kernel, int threads, size_t smem, long long work) {
+  const int sms = device_sms();
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
       per_sm <= 0) {
@@ -139,7 +145,7 @@ int vie_tucker_compress(const vie_grid* grid, double tol, int rank_rule, int fla
     set_error("unknown rank rule %d", rank_rule);
     return VIE_ERR_ARG;
   }
-  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV)) {
+  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT)) {
     set_error("unknown flags 0x%x", flags);
     return VIE_ERR_ARG;
   }
@@ -176,6 +182,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   r.max_batch = op->ws_batch;
   for (int i = 0; i < 4; ++i) r.line_threads[i] = op->tune.line_threads[i];
   r.tuned_batch = op->tune.tuned_batch;
+  r.rebuild_kernel = op->oct32 == nullptr ? 0 : (octant_uses_tc(op) ? 2 : 1);
   *info = r;
   return VIE_OK;
 }

@@ -258,6 +258,186 @@ __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
   }
 }
 
+// The same rebuild on the tensor cores (warp-level mma.sync m16n8k8, TF32
+// operands, FP32 accumulation).  A complex product C = A B is one real GEMM
+// C' = A' B': A' is A read as interleaved (re, im) floats (M x 2K), B' puts the
+// 2x2 block [[Re b, Im b], [-Im b, Re b]] in place of every entry b of B
+// (2K x 2N), and C' is C as interleaved floats.  Each operand is split into a
+// TF32 value and a TF32 remainder and the product is accumulated as
+// lo*hi + hi*lo + hi*hi (3xTF32), which keeps the rebuilt values at FP32
+// accuracy (one TF32 product alone is ~3e-4 relative).
+//
+// One warp per (component c, k1, 16 consecutive k2), two GEMMs back to back:
+//   W'  = U2_c'[k2 rows] S_c[k1]'          (M = 16, K = 2 r2, N = 2 r3)
+//   G'  = W' (U3_c^T)'                     (M = 16, K = 2 r3, N = 2 H3)
+// The accumulators of the first are the A fragments of the second, without a
+// shuffle or a trip through shared memory: inside every block of 8 the second
+// GEMM's K index is permuted (slot s < 4 is column 2s of the block, slot s >= 4
+// column 2(s-4)+1), which is exactly where a lane holds W' in its accumulator.
+// (U3_c^T)' is stored with the same permutation, once per CTA, in fragment
+// order: one 16-byte shared load per lane per (k-step, n-tile) gives the TF32
+// value and remainder of both B elements.
+constexpr int kTcThreads = 256;
+constexpr int kTcWarps = kTcThreads / 32;
+constexpr int kTcMaxKs = 8;                           // r3 <= 32
+constexpr size_t kTcSmemMax = 110u << 10;             // two CTAs per SM
+
+struct OctTcArgs {
+  OctArgs o;
+  int nk1;     // k1 values in the chunk
+  int mt;      // 16-row tiles of k2: ceil(H2 / 16)
+  int nt2;     // 8-column tiles of G': ceil(H3 / 4)
+  int nsplit;  // CTAs of a component split the n-tiles into nsplit ranges
+  int ntc;     // n-tiles per range (even)
+};
+
+__host__ __device__ constexpr int tc_ks(int r3max) { return (r3max + 3) / 4; }
+
+// n-tile ranges per component and n-tiles per range for KS k-steps
+inline void tc_split(int KS, int nt2, int* nsplit, int* ntc) {
+  for (int s = 1;; ++s) {
+    int c = (nt2 + s - 1) / s;
+    c += c & 1;
+    if ((size_t)KS * c * 32 * sizeof(float4) <= kTcSmemMax || c <= 2) {
+      *nsplit = s;
+      *ntc = c;
+      return;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = hi + lo with hi, lo TF32 (lo carries the bits hi dropped)
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(x);
+  lo = tf32_bits(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kTcThreads, 2) octant_tc_kernel(const OctTcArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint4* B2 = reinterpret_cast<uint4*>(smem_raw);     // [KS][ntc][32 lanes]
+  const int c = blockIdx.x / a.nsplit, sp = blockIdx.x - c * a.nsplit;
+  const int nt_lo = sp * a.ntc;
+  const CompMeta<float> m = a.o.meta[c];
+  const int H2 = a.o.H2, H3 = a.o.H3, r2 = m.r2, r3 = m.r3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  // (U3_c^T)' in permuted fragment order: k-step j, slot t is Re W[q], slot
+  // t + 4 is Im W[q] (q = 4 j + t); column 8 nt + g is Re (even) or Im (odd)
+  // of G[., n], n = 4 nt + g / 2.  Entries past r3 or H3 are zero.
+  for (int it = threadIdx.x; it < KS * a.ntc * 32; it += kTcThreads) {
+    const int ln = it & 31, jt = it >> 5;
+    const int j = jt / a.ntc, ntl = jt - j * a.ntc;
+    const int q = 4 * j + (ln & 3);
+    const int col = 8 * (nt_lo + ntl) + (ln >> 2), n = col >> 1;
+    float2 u = make_float2(0.f, 0.f);
+    if (q < r3 && n < H3) u = m.U3t[(long long)q * H3 + n];
+    const float b0 = (col & 1) ? u.y : u.x;            // row Re W[q]: (U3r, U3i)
+    const float b1 = (col & 1) ? u.x : -u.y;           // row Im W[q]: (-U3i, U3r)
+    uint4 v;
+    tf32_split(b0, v.x, v.z);
+    tf32_split(b1, v.y, v.w);
+    B2[it] = v;
+  }
+  __syncthreads();
+  const int units = a.nk1 * a.mt;
+  const int nt_n = min(a.ntc, a.nt2 - nt_lo);
+  const float* U2f = reinterpret_cast<const float*>(m.U2);   // [H2][2 r2]
+  const int ks1 = (2 * r2 + 7) / 8;
+  for (int u = blockIdx.y * kTcWarps + warp; u < units; u += gridDim.y * kTcWarps) {
+    const int k1l = u / a.mt, mt = u - k1l * a.mt;
+    const float2* S = m.slab + (long long)(a.o.k1a + k1l) * a.o.r2max * a.o.r3max;
+    const int row0 = mt * 16 + g, row1 = row0 + 8;
+    // GEMM 1: W' = U2' S', K index kc = 2 b + e (e: Re/Im of U2[k2, b])
+    float acc1[KS][4];
+#pragma unroll
+    for (int nt = 0; nt < KS; ++nt) acc1[nt][0] = acc1[nt][1] = acc1[nt][2] = acc1[nt][3] = 0.f;
+    for (int k = 0; k < ks1; ++k) {
+      const int kc0 = 8 * k + t, kc1 = kc0 + 4;
+      uint32_t ah[4], al[4];
+      tf32_split(row0 < H2 && kc0 < 2 * r2 ? U2f[(long long)row0 * 2 * r2 + kc0] : 0.f, ah[0], al[0]);
+      tf32_split(row1 < H2 && kc0 < 2 * r2 ? U2f[(long long)row1 * 2 * r2 + kc0] : 0.f, ah[1], al[1]);
+      tf32_split(row0 < H2 && kc1 < 2 * r2 ? U2f[(long long)row0 * 2 * r2 + kc1] : 0.f, ah[2], al[2]);
+      tf32_split(row1 < H2 && kc1 < 2 * r2 ? U2f[(long long)row1 * 2 * r2 + kc1] : 0.f, ah[3], al[3]);
+      // S' rows kc0, kc1 (b = kc >> 1, parity e = t & 1), column 8 nt + g
+      // (q = 4 nt + g / 2, parity f = g & 1): (e, f) = (0,0) Re s, (0,1) Im s,
+      // (1,0) -Im s, (1,1) Re s
+      const int b0 = kc0 >> 1, b1 = kc1 >> 1, e = t & 1, f = g & 1;
+#pragma unroll
+      for (int nt = 0; nt < KS; ++nt) {
+        const int q = 4 * nt + (g >> 1);
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+        if (q < r3) {
+          if (b0 < r2) s0 = S[b0 * a.o.r3max + q];
+          if (b1 < r2) s1 = S[b1 * a.o.r3max + q];
+        }
+        const float v0 = e == f ? s0.x : (e ? -s0.y : s0.y);
+        const float v1 = e == f ? s1.x : (e ? -s1.y : s1.y);
+        uint32_t bh0, bl0, bh1, bl1;
+        tf32_split(v0, bh0, bl0);
+        tf32_split(v1, bh1, bl1);
+        mma_tf32(acc1[nt], al, bh0, bh1);
+        mma_tf32(acc1[nt], ah, bl0, bl1);
+        mma_tf32(acc1[nt], ah, bh0, bh1);
+      }
+    }
+    // GEMM 2's A fragments: slot t <- W'[., 8 j + 2 t] (c0, c2), slot t + 4 <-
+    // W'[., 8 j + 2 t + 1] (c1, c3)
+    uint32_t a2h[KS][4], a2l[KS][4];
+#pragma unroll
+    for (int j = 0; j < KS; ++j) {
+      tf32_split(acc1[j][0], a2h[j][0], a2l[j][0]);
+      tf32_split(acc1[j][2], a2h[j][1], a2l[j][1]);
+      tf32_split(acc1[j][1], a2h[j][2], a2l[j][2]);
+      tf32_split(acc1[j][3], a2h[j][3], a2l[j][3]);
+    }
+    // GEMM 2: two n-tiles at a time, the hi*hi products and the two
+    // correction products in separate accumulators (four independent chains)
+    float2* o0 = a.o.out + (((long long)k1l * H2 + row0) * 6 + c) * H3;
+    float2* o1 = o0 + 8ll * 6 * H3;
+    for (int ntl = 0; ntl < nt_n; ntl += 2) {
+      float hh0[4] = {0.f, 0.f, 0.f, 0.f}, cr0[4] = {0.f, 0.f, 0.f, 0.f};
+      float hh1[4] = {0.f, 0.f, 0.f, 0.f}, cr1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < KS; ++j) {
+        const uint4 p = B2[(j * a.ntc + ntl) * 32 + lane];
+        const uint4 r = B2[(j * a.ntc + ntl + 1) * 32 + lane];
+        mma_tf32(cr0, a2l[j], p.x, p.y);
+        mma_tf32(cr1, a2l[j], r.x, r.y);
+        mma_tf32(cr0, a2h[j], p.z, p.w);
+        mma_tf32(cr1, a2h[j], r.z, r.w);
+        mma_tf32(hh0, a2h[j], p.x, p.y);
+        mma_tf32(hh1, a2h[j], r.x, r.y);
+      }
+      // C' columns 8 nt + 2 t, + 1 are (Re, Im) of G[k2][4 nt + t]
+      const int n0 = 4 * (nt_lo + ntl) + t, n1 = n0 + 4;
+      if (row0 < H2) {
+        if (n0 < H3) o0[n0] = make_float2(hh0[0] + cr0[0], hh0[1] + cr0[1]);
+        if (n1 < H3) o0[n1] = make_float2(hh1[0] + cr1[0], hh1[1] + cr1[1]);
+      }
+      if (row1 < H2) {
+        if (n0 < H3) o1[n0] = make_float2(hh0[2] + cr0[2], hh0[3] + cr0[3]);
+        if (n1 < H3) o1[n1] = make_float2(hh1[2] + cr1[2], hh1[3] + cr1[3]);
+      }
+    }
+  }
+}
+
+int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s);
+
 // Four-step variant (fused_fs_group) for P3 = 8 V, V = 4 R with R even.
 __host__ __device__ constexpr int fused_fs_min_blocks(int V) { return V <= 8 ? 8 : (V <= 16 ? 5 : 4); }
 
@@ -294,21 +474,9 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   // Tucker path: per chunk of k1, rebuild the half fibres (chunk 0 may already be
   // rebuilt, see matvec_run), then the groups of the chunk
   const int chunk = a.oct_chunk;
-  OctArgs o;
-  o.meta = a.meta;
-  o.r2max = a.r2max;
-  o.r3max = a.r3max;
-  o.H2 = a.H2;
-  o.H3 = a.H3;
-  o.out = const_cast<float2*>(a.octant);
-  const size_t osmem = octant_smem(a.r2max, a.r3max);
   for (int k1a = 0; k1a < a.H1; k1a += chunk) {
     const int nk1 = std::min(chunk, a.H1 - k1a);
-    o.k1a = k1a;
-    if (k1a > 0 || !a.oct_first_ready) {
-      ProfScope ps(PF_REBUILD, s);
-      octant_kernel<<<dim3((a.H2 + kOctK2 - 1) / kOctK2, nk1), 256, osmem, s>>>(o);
-    }
+    if (k1a > 0 || !a.oct_first_ready) launch_octant_args(a.op, k1a, s);
     a.oct_k1a = k1a;
     a.g0 = k1a * a.H2;
     ProfScope ps(fam, s);
@@ -447,7 +615,23 @@ vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool sto
 }
 
 int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
-  vie::OctArgs o;
+  return vie::launch_octant_args(op, k1a, s);
+}
+
+bool octant_uses_tc(const vie_op* op) {
+  return !(op->flags & VIE_REBUILD_SIMT) && vie::tc_ks(op->rmax[2]) <= vie::kTcMaxKs;
+}
+
+namespace vie {
+template <int KS>
+static void launch_tc(const OctTcArgs& t, int gy, size_t smem, cudaStream_t s) {
+  octant_tc_kernel<KS><<<dim3(6 * t.nsplit, gy), kTcThreads, smem, s>>>(t);
+}
+
+// the rebuild of chunk [k1a, k1a + oct_k1): tensor cores unless the operator
+// asked for the SIMT kernel or r3 > 32
+int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
+  OctArgs o;
   o.meta = reinterpret_cast<const CompMeta<float>*>(op->meta);
   o.r2max = op->rmax[1];
   o.r3max = op->rmax[2];
@@ -456,12 +640,38 @@ int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
   o.k1a = k1a;
   o.out = op->oct32;
   const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
-  const size_t osmem = vie::octant_smem(o.r2max, o.r3max);
   ProfScope ps(PF_REBUILD, s);
-  vie::octant_kernel<<<dim3((o.H2 + vie::kOctK2 - 1) / vie::kOctK2, nk1), 256, osmem, s>>>(o);
+  if (octant_uses_tc(op)) {
+    OctTcArgs t;
+    t.o = o;
+    t.nk1 = nk1;
+    t.mt = (o.H2 + 15) / 16;
+    t.nt2 = (o.H3 + 3) / 4;
+    const int KS = tc_ks(o.r3max);
+    tc_split(KS, t.nt2, &t.nsplit, &t.ntc);
+    const size_t smem = (size_t)KS * t.ntc * 32 * sizeof(float4);
+    // about one unit of 16 k2 rows per warp, at most two CTAs per SM
+    const int units = nk1 * t.mt;
+    const int gcap = std::max(1, 2 * device_sms() / (6 * t.nsplit));
+    const int gy = std::max(1, std::min((units + kTcWarps - 1) / kTcWarps, gcap));
+    switch (KS) {
+      case 1: launch_tc<1>(t, gy, smem, s); break;
+      case 2: launch_tc<2>(t, gy, smem, s); break;
+      case 3: launch_tc<3>(t, gy, smem, s); break;
+      case 4: launch_tc<4>(t, gy, smem, s); break;
+      case 5: launch_tc<5>(t, gy, smem, s); break;
+      case 6: launch_tc<6>(t, gy, smem, s); break;
+      case 7: launch_tc<7>(t, gy, smem, s); break;
+      default: launch_tc<8>(t, gy, smem, s); break;
+    }
+  } else {
+    const size_t osmem = octant_smem(o.r2max, o.r3max);
+    octant_kernel<<<dim3((o.H2 + kOctK2 - 1) / kOctK2, nk1), 256, osmem, s>>>(o);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "rebuild launch");
 }
+}  // namespace vie
 
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
@@ -471,6 +681,7 @@ int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* a
     if (!stored && op->oct32 != nullptr) {
       a.octant = op->oct32;
       a.oct_chunk = op->oct_k1;
+      a.op = op;
       a.oct_first_ready = first_chunk_ready;
     }
   }
@@ -497,6 +708,14 @@ int fused_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<24, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::fused_fs_kernel<24, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   // octant_kernel also holds the six metadata records in static shared memory
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");

@@ -286,6 +286,8 @@ __host__ __device__ constexpr size_t octant_smem_bytes(int r2max, int r3max) {
   return (size_t)(6 * r3max * kOctantK2 + 6 * r2max * r3max + 6 * kOctantK2 * r2max) * sizeof(float2);
 }
 int launch_octant(const vie_op* op, int k1a, cudaStream_t s);
+// the rebuild runs on the tensor cores (octant_tc_kernel), else on the SIMT octant_kernel
+bool octant_uses_tc(const vie_op* op);
 
 // setup internals (setup.cu)
 int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,
@@ -295,6 +297,7 @@ int op_tables(vie_op* op);   // FFT plans and root tables of op->P
 int line_fft_init_attributes();
 // persistent grid size for `kernel` with `threads` threads and `smem` bytes of
 // dynamic shared memory: resident CTAs per SM x SMs, capped by `work`
+int device_sms();
 int persistent_grid(const void* kernel, int threads, size_t smem, long long work);
 int fused_init_attributes();
 int multi_init_attributes();

@@ -135,6 +135,31 @@ def test_matvec_register_fft_radices(n):
     assert rel(host(op.matvec_adjoint(dev(y))), AD.adjoint_matvec(rebuilt, y)) <= 1e-5
 
 
+@pytest.mark.parametrize("n,tol", [((16, 16, 16), 1e-8), ((20, 9, 32), 1e-6), ((6, 10, 48), 1e-10),
+                                   ((35, 25, 64), 1e-4)])
+def test_rebuild_tensor_cores_and_simt(n, tol):
+    """Both rebuilds of the half fibres of eq. (13) into the scratch, the 3xTF32
+    tensor-core GEMMs and the FP32 FMA kernel, against the oracle's HOSVD.
+    The grids give ragged k2 tiles (H2 = 9, 10, 6, 26 rows against tiles of 16), r3 from a few
+    to past 32 (where the tensor-core kernel hands over to the FMA one)."""
+    Ghat = E.green_spectra(K.toeplitz_tensor(*n, HVOX, K0), *n)
+    rebuilt = H.rebuild_components(H.compress_components(Ghat, tol, "tail"))
+    J = rand_field(n, B=3, seed=5)
+    ref = M.matvec_fft(rebuilt, J)
+    outs = {}
+    for kind in ("tensor_cores", "simt"):
+        op = vie.Operator(n, HVOX, F, tol, rebuild=kind)
+        info = op.info()
+        r3 = max(r[2] for r in info["ranks"])
+        want = "tensor_cores" if kind == "tensor_cores" and r3 <= 32 else "simt"
+        assert info["rebuild_kernel"] == want
+        assert info["rebuild_scratch_bytes"] > 0
+        outs[kind] = host(op.matvec(dev(J)))
+        assert rel(outs[kind], ref) <= 1e-5, kind
+        op.close()
+    assert rel(outs["tensor_cores"], outs["simt"]) <= 1e-5
+
+
 @pytest.mark.parametrize("n", [(3, 4, 5), (6, 10, 20), (16, 16, 16)])
 def test_matvec_uncompressed_paths(n):
     T, Ghat, comp, rebuilt, op = setup_case(n)
