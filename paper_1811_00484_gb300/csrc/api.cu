@@ -428,6 +428,7 @@ void vie_destroy(vie_op* op) {
   cudaFree(op->slab32);
   cudaFree(op->slab64);
   cudaFree(op->oct32);
+  cudaFree(op->u3frag);
   cudaFree(op->spec32);
   cudaFree(op->spec64);
   for (int q = 0; q < 3; ++q) {

@@ -274,31 +274,47 @@ __global__ void __launch_bounds__(256) octant_kernel(const OctArgs a) {
 // shuffle or a trip through shared memory: inside every block of 8 the second
 // GEMM's K index is permuted (slot s < 4 is column 2s of the block, slot s >= 4
 // column 2(s-4)+1), which is exactly where a lane holds W' in its accumulator.
-// (U3_c^T)' is stored with the same permutation, once per CTA, in fragment
-// order: one 16-byte shared load per lane per (k-step, n-tile) gives the TF32
-// value and remainder of both B elements.
-constexpr int kTcThreads = 256;
+// (U3_c^T)' is stored with the same permutation in fragment order, split at
+// setup (u3frag_kernel): one 16-byte shared load per lane per (k-step, n-tile)
+// gives the TF32 value and remainder of both B elements.
+//
+// The last k2 tile holds H2 mod 16 rows (one, the Nyquist row, when P2 is a
+// multiple of 32); up to kTcSimtRows such rows are rebuilt with FP32 FMAs by
+// one warp instead of a mostly empty mma tile.
+//
+// One CTA per SM: a CTA takes an equal, contiguous range of (k1, k2-tile)
+// units of one component (and one range of n-tiles), so the slab cores it
+// needs are a few consecutive k1; it stages them, the U2 rows and the U3
+// fragments with cp.async in one round trip, then each warp runs its units
+// from shared memory.
+constexpr int kTcThreads = 512;
+constexpr int kTcSimtRows = 4;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kTcMaxKs = 8;                           // r3 <= 32
-constexpr size_t kTcSmemMax = 110u << 10;             // two CTAs per SM
+constexpr size_t kTcFragMax = 72u << 10;              // U3 fragments per CTA
 
 struct OctTcArgs {
   OctArgs o;
-  int nk1;     // k1 values in the chunk
-  int mt;      // 16-row tiles of k2: ceil(H2 / 16)
-  int nt2;     // 8-column tiles of G': ceil(H3 / 4)
-  int nsplit;  // CTAs of a component split the n-tiles into nsplit ranges
-  int ntc;     // n-tiles per range (even)
+  const uint4* frag;  // [6][nsplit][KS][ntc][32]
+  int nk1;            // k1 values in the chunk
+  int mt;             // 16-row tiles of k2: ceil(H2 / 16)
+  int nt2;            // 8-column tiles of G': ceil(H3 / 4)
+  int nsplit;         // CTAs of a component split the n-tiles into nsplit ranges
+  int ntc;            // n-tiles per range (even)
+  int per;            // units per CTA
+  int kspan;          // k1 rows of slab cores a CTA stages
+  int la;             // row stride (floats) of the staged U2 rows
+  int ks1m;           // k-steps of GEMM 1 for r2max: ceil(r2max / 4)
 };
 
-__host__ __device__ constexpr int tc_ks(int r3max) { return (r3max + 3) / 4; }
+__host__ __device__ constexpr int tc_ks(int r) { return (r + 3) / 4; }
 
 // n-tile ranges per component and n-tiles per range for KS k-steps
 inline void tc_split(int KS, int nt2, int* nsplit, int* ntc) {
   for (int s = 1;; ++s) {
     int c = (nt2 + s - 1) / s;
     c += c & 1;
-    if ((size_t)KS * c * 32 * sizeof(float4) <= kTcSmemMax || c <= 2) {
+    if ((size_t)KS * c * 32 * sizeof(uint4) <= kTcFragMax || c <= 2) {
       *nsplit = s;
       *ntc = c;
       return;
@@ -326,41 +342,140 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// (U3_c^T)' fragments: k-step j, slot t is Re W[q], slot t + 4 is Im W[q]
+// (q = 4 j + t); column 8 nt + g is Re (even) or Im (odd) of G[., n],
+// n = 4 nt + g / 2; entries past r3 or H3 are zero.  uint4 = (hi b0, hi b1,
+// lo b0, lo b1).
+__global__ void u3frag_kernel(const CompMeta<float>* meta, int KS, int nsplit, int ntc, int H3,
+                              uint4* out) {
+  const long long blk = (long long)KS * ntc * 32, per = nsplit * blk;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * per) return;
+  const int c = (int)(i / per);
+  long long r = i - c * per;
+  const int sp = (int)(r / blk);
+  r -= sp * blk;
+  const int ln = (int)(r & 31), jt = (int)(r >> 5);
+  const int j = jt / ntc, ntl = jt - j * ntc;
+  const CompMeta<float> m = meta[c];
+  const int q = 4 * j + (ln & 3);
+  const int col = 8 * (sp * ntc + ntl) + (ln >> 2), n = col >> 1;
+  float2 u = make_float2(0.f, 0.f);
+  if (q < m.r3 && n < H3) u = m.U3t[(long long)q * H3 + n];
+  const float b0 = (col & 1) ? u.y : u.x;            // row Re W[q]: (U3r, U3i)
+  const float b1 = (col & 1) ? u.x : -u.y;           // row Im W[q]: (-U3i, U3r)
+  uint4 v;
+  tf32_split(b0, v.x, v.z);
+  tf32_split(b1, v.y, v.w);
+  out[i] = v;
+}
+
 template <int KS>
-__global__ void __launch_bounds__(kTcThreads, 2) octant_tc_kernel(const OctTcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) octant_tc_kernel(const OctTcArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint4* B2 = reinterpret_cast<uint4*>(smem_raw);     // [KS][ntc][32 lanes]
   const int c = blockIdx.x / a.nsplit, sp = blockIdx.x - c * a.nsplit;
-  const int nt_lo = sp * a.ntc;
   const CompMeta<float> m = a.o.meta[c];
-  const int H2 = a.o.H2, H3 = a.o.H3, r2 = m.r2, r3 = m.r3;
+  const int H2 = a.o.H2, H3 = a.o.H3, r2 = m.r2, r3 = m.r3, r2m = a.o.r2max, r3m = a.o.r3max;
+  const int units = a.nk1 * a.mt;
+  const int u0 = blockIdx.y * a.per, u1 = min(units, u0 + a.per);
+  if (u0 >= u1) return;
+  const int k1lo = u0 / a.mt, kspan = (u1 - 1) / a.mt - k1lo + 1;
+  const int LA = a.la, rows = a.mt * 16, ks1m = a.ks1m, ncols = 4 * a.ntc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  // (U3_c^T)' in permuted fragment order: k-step j, slot t is Re W[q], slot
-  // t + 4 is Im W[q] (q = 4 j + t); column 8 nt + g is Re (even) or Im (odd)
-  // of G[., n], n = 4 nt + g / 2.  Entries past r3 or H3 are zero.
-  for (int it = threadIdx.x; it < KS * a.ntc * 32; it += kTcThreads) {
-    const int ln = it & 31, jt = it >> 5;
-    const int j = jt / a.ntc, ntl = jt - j * a.ntc;
-    const int q = 4 * j + (ln & 3);
-    const int col = 8 * (nt_lo + ntl) + (ln >> 2), n = col >> 1;
-    float2 u = make_float2(0.f, 0.f);
-    if (q < r3 && n < H3) u = m.U3t[(long long)q * H3 + n];
-    const float b0 = (col & 1) ? u.y : u.x;            // row Re W[q]: (U3r, U3i)
-    const float b1 = (col & 1) ? u.x : -u.y;           // row Im W[q]: (-U3i, U3r)
-    uint4 v;
-    tf32_split(b0, v.x, v.z);
-    tf32_split(b1, v.y, v.w);
-    B2[it] = v;
+  const int nt_lo = sp * a.ntc, nt_n = min(a.ntc, a.nt2 - nt_lo);
+  uint4* B2 = reinterpret_cast<uint4*>(smem_raw);                // [KS][ntc][32]
+  uint4* B1 = B2 + KS * a.ntc * 32;                               // [kspan][ks1m][KS][32]
+  float* U2s = reinterpret_cast<float*>(B1 + a.kspan * ks1m * KS * 32);   // [mt 16][LA]
+  float2* Ss = reinterpret_cast<float2*>(U2s + rows * LA);       // [kspan][r2max][r3max]
+  float2* U3s = Ss + a.kspan * r2m * r3m;                        // [r3max][4 ntc]: U3[n0 + i, q]
+  {
+    const uint4* fr = a.frag + ((long long)c * a.nsplit + sp) * KS * a.ntc * 32;
+    for (int i = threadIdx.x; i < KS * a.ntc * 32; i += kTcThreads) cp_async16(B2 + i, fr + i);
+    const float2* U2 = m.U2;                                      // [H2][r2]
+    const int half = LA / 2;                                      // float2 per staged row
+    for (int i = threadIdx.x; i < rows * half; i += kTcThreads) {
+      const int k2 = i / half, b = i - k2 * half;
+      float2* d = reinterpret_cast<float2*>(U2s + k2 * LA) + b;
+      if (k2 < H2 && b < r2) cp_async8(d, U2 + (long long)k2 * r2 + b);
+      else *d = make_float2(0.f, 0.f);
+    }
+    const float2* S = m.slab + (long long)(a.o.k1a + k1lo) * r2m * r3m;
+    for (int i = threadIdx.x; i < kspan * r2m * r3m; i += kTcThreads) cp_async8(Ss + i, S + i);
+    for (int i = threadIdx.x; i < r3m * ncols; i += kTcThreads) {
+      const int q = i / ncols, n = 4 * nt_lo + (i - q * ncols);
+      if (q < r3 && n < H3) cp_async8(U3s + i, m.U3t + (long long)q * H3 + n);
+      else U3s[i] = make_float2(0.f, 0.f);
+    }
+    cp_async_wait_all();
   }
   __syncthreads();
-  const int units = a.nk1 * a.mt;
-  const int nt_n = min(a.ntc, a.nt2 - nt_lo);
-  const float* U2f = reinterpret_cast<const float*>(m.U2);   // [H2][2 r2]
+  // S' fragments of GEMM 1 for every staged k1: rows kc0 = 8 k + t and
+  // kc1 = kc0 + 4 (b = kc >> 1, parity e = t & 1), column 8 nt + g (q =
+  // 4 nt + g / 2, parity f = g & 1): (e, f) = (0,0) Re s, (0,1) Im s,
+  // (1,0) -Im s, (1,1) Re s.  uint4 = (hi v0, hi v1, lo v0, lo v1).
+  for (int i = threadIdx.x; i < kspan * ks1m * KS * 32; i += kTcThreads) {
+    const int ln = i & 31, r = i >> 5;
+    const int nt = r % KS, k = (r / KS) % ks1m, kk = r / (KS * ks1m);
+    const int tt = ln & 3, gg = ln >> 2;
+    const int b0 = (8 * k + tt) >> 1, b1 = b0 + 2, e = tt & 1, f = gg & 1;
+    const int q = 4 * nt + (gg >> 1);
+    const float2* Sk = Ss + kk * r2m * r3m;
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+    if (q < r3) {
+      if (b0 < r2) s0 = Sk[b0 * r3m + q];
+      if (b1 < r2) s1 = Sk[b1 * r3m + q];
+    }
+    const float v0 = e == f ? s0.x : (e ? -s0.y : s0.y);
+    const float v1 = e == f ? s1.x : (e ? -s1.y : s1.y);
+    uint4 v;
+    tf32_split(v0, v.x, v.z);
+    tf32_split(v1, v.y, v.w);
+    B1[i] = v;
+  }
+  __syncthreads();
   const int ks1 = (2 * r2 + 7) / 8;
-  for (int u = blockIdx.y * kTcWarps + warp; u < units; u += gridDim.y * kTcWarps) {
+  const int rem = H2 - 16 * (H2 / 16);                 // rows of the last, partial tile
+  for (int u = u0 + warp; u < u1; u += kTcWarps) {
     const int k1l = u / a.mt, mt = u - k1l * a.mt;
-    const float2* S = m.slab + (long long)(a.o.k1a + k1l) * a.o.r2max * a.o.r3max;
+    if (rem > 0 && rem <= kTcSimtRows && mt == a.mt - 1) {
+      // W[q] = sum_b U2[k2, b] S[b, q] with q = lane, then G[k2, n] =
+      // sum_q W[q] U3[n, q] for this CTA's n range, W broadcast by shuffles
+      const float2* S = Ss + (k1l - k1lo) * r2m * r3m;
+      const int nb = 4 * nt_lo, ne = min(H3, 4 * (nt_lo + nt_n));
+      for (int k2 = 16 * mt; k2 < H2; ++k2) {
+        const float2* u2 = reinterpret_cast<const float2*>(U2s + k2 * LA);
+        float2 w = make_float2(0.f, 0.f);
+        if (lane < r3)
+          for (int b = 0; b < r2; ++b) w = cmadd(u2[b], S[b * r3m + lane], w);
+        float2* orow = a.o.out + (((long long)k1l * H2 + k2) * 6 + c) * H3;
+        for (int n0 = nb; n0 < ne; n0 += 32) {
+          const int n = n0 + lane;
+          float2 acc = make_float2(0.f, 0.f);
+          for (int q = 0; q < r3; ++q) {
+            const float2 wq = make_float2(__shfl_sync(0xffffffffu, w.x, q), __shfl_sync(0xffffffffu, w.y, q));
+            if (n < ne) acc = cmadd(wq, U3s[q * ncols + (n - nb)], acc);
+          }
+          if (n < ne) orow[n] = acc;
+        }
+      }
+      continue;
+    }
+    const uint4* B1k = B1 + (k1l - k1lo) * ks1m * KS * 32 + lane;
     const int row0 = mt * 16 + g, row1 = row0 + 8;
+    const float* A0 = U2s + row0 * LA;
+    const float* A1 = A0 + 8 * LA;
     // GEMM 1: W' = U2' S', K index kc = 2 b + e (e: Re/Im of U2[k2, b])
     float acc1[KS][4];
 #pragma unroll
@@ -368,30 +483,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) octant_tc_kernel(const OctTcArg
     for (int k = 0; k < ks1; ++k) {
       const int kc0 = 8 * k + t, kc1 = kc0 + 4;
       uint32_t ah[4], al[4];
-      tf32_split(row0 < H2 && kc0 < 2 * r2 ? U2f[(long long)row0 * 2 * r2 + kc0] : 0.f, ah[0], al[0]);
-      tf32_split(row1 < H2 && kc0 < 2 * r2 ? U2f[(long long)row1 * 2 * r2 + kc0] : 0.f, ah[1], al[1]);
-      tf32_split(row0 < H2 && kc1 < 2 * r2 ? U2f[(long long)row0 * 2 * r2 + kc1] : 0.f, ah[2], al[2]);
-      tf32_split(row1 < H2 && kc1 < 2 * r2 ? U2f[(long long)row1 * 2 * r2 + kc1] : 0.f, ah[3], al[3]);
-      // S' rows kc0, kc1 (b = kc >> 1, parity e = t & 1), column 8 nt + g
-      // (q = 4 nt + g / 2, parity f = g & 1): (e, f) = (0,0) Re s, (0,1) Im s,
-      // (1,0) -Im s, (1,1) Re s
-      const int b0 = kc0 >> 1, b1 = kc1 >> 1, e = t & 1, f = g & 1;
+      tf32_split(A0[kc0], ah[0], al[0]);
+      tf32_split(A1[kc0], ah[1], al[1]);
+      tf32_split(A0[kc1], ah[2], al[2]);
+      tf32_split(A1[kc1], ah[3], al[3]);
 #pragma unroll
       for (int nt = 0; nt < KS; ++nt) {
-        const int q = 4 * nt + (g >> 1);
-        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
-        if (q < r3) {
-          if (b0 < r2) s0 = S[b0 * a.o.r3max + q];
-          if (b1 < r2) s1 = S[b1 * a.o.r3max + q];
-        }
-        const float v0 = e == f ? s0.x : (e ? -s0.y : s0.y);
-        const float v1 = e == f ? s1.x : (e ? -s1.y : s1.y);
-        uint32_t bh0, bl0, bh1, bl1;
-        tf32_split(v0, bh0, bl0);
-        tf32_split(v1, bh1, bl1);
-        mma_tf32(acc1[nt], al, bh0, bh1);
-        mma_tf32(acc1[nt], ah, bl0, bl1);
-        mma_tf32(acc1[nt], ah, bh0, bh1);
+        const uint4 bv = B1k[(k * KS + nt) * 32];
+        mma_tf32(acc1[nt], al, bv.x, bv.y);
+        mma_tf32(acc1[nt], ah, bv.z, bv.w);
+        mma_tf32(acc1[nt], ah, bv.x, bv.y);
       }
     }
     // GEMM 2's A fragments: slot t <- W'[., 8 j + 2 t] (c0, c2), slot t + 4 <-
@@ -618,8 +719,11 @@ int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
   return vie::launch_octant_args(op, k1a, s);
 }
 
-bool octant_uses_tc(const vie_op* op) {
-  return !(op->flags & VIE_REBUILD_SIMT) && vie::tc_ks(op->rmax[2]) <= vie::kTcMaxKs;
+bool octant_uses_tc(const vie_op* op) { return op->u3frag != nullptr; }
+
+bool tc_rebuild_eligible(const vie_op* op) {
+  return op->oct32 != nullptr && !(op->flags & VIE_REBUILD_SIMT) &&
+         vie::tc_ks(op->rmax[2]) <= vie::kTcMaxKs;
 }
 
 namespace vie {
@@ -628,9 +732,37 @@ static void launch_tc(const OctTcArgs& t, int gy, size_t smem, cudaStream_t s) {
   octant_tc_kernel<KS><<<dim3(6 * t.nsplit, gy), kTcThreads, smem, s>>>(t);
 }
 
-// the rebuild of chunk [k1a, k1a + oct_k1): tensor cores unless the operator
-// asked for the SIMT kernel or r3 > 32
-int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
+constexpr size_t kTcSmemLimit = 227u << 10;
+
+// launch shape of octant_tc_kernel for nk1 values of k1; returns its shared memory
+static size_t tc_plan(const vie_op* op, const OctArgs& o, int nk1, OctTcArgs* t) {
+  t->o = o;
+  t->frag = op->u3frag;
+  t->nk1 = nk1;
+  t->mt = (o.H2 + 15) / 16;
+  t->nt2 = (o.H3 + 3) / 4;
+  t->nsplit = op->tc_nsplit;
+  t->ntc = op->tc_ntc;
+  t->la = 8 * tc_ks(o.r2max) + 4;                     // >= 2 r2max, 4 mod 8: no bank conflicts
+  t->ks1m = tc_ks(o.r2max);
+  // one CTA per SM with equal unit ranges; more, smaller ranges when the
+  // staged slab cores would not fit
+  const int units = nk1 * t->mt;
+  int gy = std::max(1, std::min((units + kTcWarps - 1) / kTcWarps, device_sms() / (6 * t->nsplit)));
+  for (;;) {
+    t->per = (units + gy - 1) / gy;
+    t->kspan = (t->per + t->mt - 1) / t->mt + 1;
+    const size_t smem = (size_t)op->tc_ks * t->ntc * 32 * sizeof(uint4) +
+                        (size_t)t->kspan * t->ks1m * op->tc_ks * 32 * sizeof(uint4) +
+                        (size_t)t->mt * 16 * t->la * sizeof(float) +
+                        (size_t)t->kspan * o.r2max * o.r3max * sizeof(float2) +
+                        (size_t)o.r3max * 4 * t->ntc * sizeof(float2);
+    if (smem <= kTcSmemLimit || t->per == 1) return smem;
+    gy = std::min(units, 2 * gy);
+  }
+}
+
+static OctArgs octant_args(const vie_op* op, int k1a) {
   OctArgs o;
   o.meta = reinterpret_cast<const CompMeta<float>*>(op->meta);
   o.r2max = op->rmax[1];
@@ -639,21 +771,20 @@ int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
   o.H3 = op->H[2];
   o.k1a = k1a;
   o.out = op->oct32;
+  return o;
+}
+
+// the rebuild of chunk [k1a, k1a + oct_k1): tensor cores when the operator
+// holds the U3 fragments (r3 <= 32 and no VIE_REBUILD_SIMT), else FMAs
+int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
+  const OctArgs o = octant_args(op, k1a);
   const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
   ProfScope ps(PF_REBUILD, s);
-  if (octant_uses_tc(op)) {
-    OctTcArgs t;
-    t.o = o;
-    t.nk1 = nk1;
-    t.mt = (o.H2 + 15) / 16;
-    t.nt2 = (o.H3 + 3) / 4;
-    const int KS = tc_ks(o.r3max);
-    tc_split(KS, t.nt2, &t.nsplit, &t.ntc);
-    const size_t smem = (size_t)KS * t.ntc * 32 * sizeof(float4);
-    // about one unit of 16 k2 rows per warp, at most two CTAs per SM
-    const int units = nk1 * t.mt;
-    const int gcap = std::max(1, 2 * device_sms() / (6 * t.nsplit));
-    const int gy = std::max(1, std::min((units + kTcWarps - 1) / kTcWarps, gcap));
+  OctTcArgs t;
+  const size_t smem = op->u3frag != nullptr ? tc_plan(op, o, nk1, &t) : 0;
+  if (op->u3frag != nullptr && smem <= kTcSmemLimit) {
+    const int KS = op->tc_ks;
+    const int gy = (nk1 * t.mt + t.per - 1) / t.per;   // every CTA has a unit
     switch (KS) {
       case 1: launch_tc<1>(t, gy, smem, s); break;
       case 2: launch_tc<2>(t, gy, smem, s); break;
@@ -672,6 +803,27 @@ int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "rebuild launch");
 }
 }  // namespace vie
+
+void tc_layout(int r3max, int H3, int* ks, int* nsplit, int* ntc) {
+  *ks = vie::tc_ks(r3max);
+  vie::tc_split(*ks, (H3 + 3) / 4, nsplit, ntc);
+}
+
+// the largest chunk's launch fits in shared memory (op->tc_* already set)
+bool tc_rebuild_fits(const vie_op* op) {
+  vie::OctTcArgs t;
+  return vie::tc_plan(op, vie::octant_args(op, 0), op->oct_k1, &t) <= vie::kTcSmemLimit;
+}
+
+int launch_u3_fragments(const vie_op* op, cudaStream_t s) {
+  const long long n = 6ll * op->tc_nsplit * op->tc_ks * op->tc_ntc * 32;
+  vie::u3frag_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const CompMeta<float>*>(op->meta), op->tc_ks, op->tc_nsplit, op->tc_ntc,
+      op->H[2], op->u3frag);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "U3 fragment launch");
+}
+
 
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,

@@ -620,6 +620,13 @@ static int finish_operator(vie_op* op) {
     VIE_CUDA(cudaStreamCreateWithFlags(&op->rb_stream, cudaStreamNonBlocking));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_fork, cudaEventDisableTiming));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_join, cudaEventDisableTiming));
+    if (tc_rebuild_eligible(op)) {
+      tc_layout(op->rmax[2], op->H[2], &op->tc_ks, &op->tc_nsplit, &op->tc_ntc);
+    }
+    if (op->tc_ks > 0 && tc_rebuild_fits(op)) {
+      VIE_TRY(dalloc(&op->u3frag, 6ull * op->tc_nsplit * op->tc_ks * op->tc_ntc * 32 * sizeof(uint4)));
+      VIE_TRY(launch_u3_fragments(op, 0));
+    }
   }
   VIE_CUDA(cudaDeviceSynchronize());
   return VIE_OK;

@@ -200,6 +200,10 @@ struct vie_op {
   // host-side, in launch order: chunk 0 of the next matvec's rebuild is already
   // enqueued on rb_stream (started by the previous matvec, see MV_PREFETCH_REBUILD)
   bool rb_pending = false;
+  // tensor-core rebuild: the real form of U3^T, split into TF32 value and
+  // remainder, in mma fragment order [6][tc_nsplit][tc_ks][tc_ntc][32]
+  uint4* u3frag = nullptr;
+  int tc_ks = 0, tc_nsplit = 0, tc_ntc = 0;
   // stored spectra (optional)
   float2* spec32 = nullptr;  double2* spec64 = nullptr;
   FftPlan plan[3];
@@ -286,8 +290,13 @@ __host__ __device__ constexpr size_t octant_smem_bytes(int r2max, int r3max) {
   return (size_t)(6 * r3max * kOctantK2 + 6 * r2max * r3max + 6 * kOctantK2 * r2max) * sizeof(float2);
 }
 int launch_octant(const vie_op* op, int k1a, cudaStream_t s);
-// the rebuild runs on the tensor cores (octant_tc_kernel), else on the SIMT octant_kernel
+// the rebuild runs on the tensor cores (octant_tc_kernel, when the operator
+// holds the U3 fragments), else on the FP32-FMA octant_kernel
 bool octant_uses_tc(const vie_op* op);
+bool tc_rebuild_eligible(const vie_op* op);
+void tc_layout(int r3max, int H3, int* ks, int* nsplit, int* ntc);
+bool tc_rebuild_fits(const vie_op* op);
+int launch_u3_fragments(const vie_op* op, cudaStream_t s);
 
 // setup internals (setup.cu)
 int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,
