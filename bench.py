@@ -47,6 +47,8 @@ def parse():
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
+    p.add_argument("--rebuild", default="tensor_cores", choices=["tensor_cores", "simt"],
+                   help="matvec / solve1: how the Tucker path rebuilds the Green's fibres")
     p.add_argument("--record-traffic", metavar="NCU_CSV",
                    help="turn an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum per launch "
                         "into the row of --family in profiles/roofline_traffic.md, then exit")
@@ -274,7 +276,8 @@ def run_solve1_mode(args):
     import workloads
 
     wl = workloads.solve_n64() if args.n == 64 else workloads.make("custom", args.n, 1, incident="plane")
-    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed")
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed",
+                      rebuild=args.rebuild)
     chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
     einc = torch.from_numpy(wl.einc.astype(np.complex64)).cuda()
     kw = dict(tol=1e-6, restart=50, path=args.path, use_graph=not args.no_graph, orth=args.orth)
@@ -287,7 +290,8 @@ def run_solve1_mode(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    print(json.dumps({"mode": "solve1", "n": args.n, "path": args.path, "graph": not args.no_graph,
+    print(json.dumps({"mode": "solve1", "n": args.n, "path": args.path, "rebuild": op.info()["rebuild_kernel"],
+                      "graph": not args.no_graph,
                       "orth": args.orth, "ms_per_solve": 1e3 * el / args.steps,
                       "iterations": infos[-1]["iterations"], "refine_steps": infos[-1]["refine_steps"],
                       "relres": infos[-1]["relres"],
@@ -303,7 +307,8 @@ def run_matvec_mode(args):
     import workloads
 
     wl = workloads.make("matvec", args.n, seed=1, B=args.batch, tol_svd=1e-6)
-    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed")
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=args.path == "uncompressed",
+                      rebuild=args.rebuild)
     J = torch.from_numpy(wl.J.astype(np.complex64)).cuda()
     Y = torch.empty_like(J)
     for _ in range(args.warmup):
@@ -319,6 +324,7 @@ def run_matvec_mode(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
     print(json.dumps({"mode": "matvec", "n": args.n, "batch": args.batch, "path": args.path,
+                      "rebuild": op.info()["rebuild_kernel"],
                       "ms_per_matvec_batch": ms, "matvecs_per_s": args.batch / (ms * 1e-3)}))
 
 

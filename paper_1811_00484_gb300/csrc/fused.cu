@@ -748,7 +748,7 @@ static size_t tc_plan(const vie_op* op, const OctArgs& o, int nk1, OctTcArgs* t)
   // one CTA per SM with equal unit ranges; more, smaller ranges when the
   // staged slab cores would not fit
   const int units = nk1 * t->mt;
-  int gy = std::max(1, std::min((units + kTcWarps - 1) / kTcWarps, device_sms() / (6 * t->nsplit)));
+  int gy = std::max(1, std::min(units, device_sms() / (6 * t->nsplit)));
   for (;;) {
     t->per = (units + gy - 1) / gy;
     t->kspan = (t->per + t->mt - 1) / t->mt + 1;
