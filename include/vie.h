@@ -65,7 +65,8 @@ typedef enum vie_status {
 } vie_status;
 
 enum { VIE_C64 = 0, VIE_C128 = 1 };                 /* array precision          */
-enum { VIE_PATH_TUCKER = 0, VIE_PATH_UNCOMPRESSED = 1 };
+enum { VIE_PATH_TUCKER = 0, VIE_PATH_UNCOMPRESSED = 1,
+       VIE_PATH_TUCKER_CP = 2 };            /* after vie_tucker_cp; FP32 only */
 
 /* HOSVD truncation rule (Algorithm 1; the printed rule is garbled):
  * TAIL      - smallest r_q with sqrt(sum_{j>r_q} sigma_j^2) <= (tol/sqrt3)||A||_F,
@@ -124,6 +125,13 @@ typedef struct vie_op_info_t {
                                     half fibres: 0 inside the fused z-stage
                                     CTAs (no scratch), 1 FP32 FMAs into the
                                     scratch, 2 tensor cores (3xTF32) into it    */
+    int cp_rank;                 /* terms R of the Tucker+CP model (0: none)   */
+    double cp_rel_err[6];        /* ||core - CP|| / ||core|| per component;
+                                    the factors U^q are orthonormal, so this
+                                    is also the Tucker+CP error relative to
+                                    the Tucker model                           */
+    int cp_sweeps[6];            /* ALS sweeps taken per component             */
+    size_t cp_bytes;             /* c64 Tucker+CP factors W^q (half rows)      */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */
@@ -178,6 +186,34 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info);
 int vie_op_export(const vie_op* op, int c, double* core, double* U1, double* U2,
                   double* U3, double* sigma1, double* sigma2, double* sigma3,
                   void* stream);
+
+/*
+ * Tucker+CP (Algorithm 2): a CP model with `rank` terms (1..32) of each of
+ * the six HOSVD cores of `op`, core ~ sum_l V1[:, l] o V2[:, l] o V3[:, l],
+ * fitted by alternating least squares on the device in FP64 (each sweep
+ * solves the least-squares problem of V1, V2, V3 in turn with the other two
+ * fixed), from a start fixed by `seed`; sweeps stop when the relative core
+ * error changes by less than `tol`, or after `max_iter` sweeps.  Then the
+ * Tucker+CP factors W^q = U^q V^q (eq. (17)) are formed, and the FP32
+ * matvec, adjoint matvec and solve accept VIE_PATH_TUCKER_CP, which rebuilds
+ * the half fibres from eq. (17) at every matvec (in a solve, FP64
+ * refinement residuals use the Tucker model).  Calling it again replaces the
+ * model.  Needs the rebuild scratch (rebuild_kernel != 0 in vie_op_info).
+ * Errors: VIE_ERR_ARG (rank, tol, max_iter, a Tucker rank above 64, no
+ * scratch), VIE_ERR_NUMERIC (the fit did not stay finite), VIE_ERR_OOM.
+ * Synchronises `stream`.
+ */
+int vie_tucker_cp(vie_op* op, int rank, double tol, int max_iter,
+                  unsigned long long seed, void* stream);
+
+/*
+ * Tucker+CP factors of component c to host buffers in c128, W1 [P1][R],
+ * W2 [P2][R], W3 [P3][R] (all P_q rows, so that eq. (17) rebuilds the full
+ * spectrum), the final relative core error and the sweeps taken.  Any
+ * pointer may be NULL.  VIE_ERR_ARG without a model.  Synchronises `stream`.
+ */
+int vie_cp_export(const vie_op* op, int c, double* W1, double* W2, double* W3,
+                  double* rel_err, int* sweeps, void* stream);
 
 /*
  * The uncompressed FFT'd circulant component c (Section V.A) for `grid`,

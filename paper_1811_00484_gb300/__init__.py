@@ -25,7 +25,7 @@ VIE_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
           4: "no convergence", 5: "numerical failure", 6: "device wait timed out"}
 VIE_C64, VIE_C128 = 0, 1
-PATHS = {"tucker": 0, "uncompressed": 1}
+PATHS = {"tucker": 0, "uncompressed": 1, "tucker_cp": 2}
 RANK_RULES = {"tail": 0, "sigma_max": 1}
 VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT = 1, 2, 4
 REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "tensor_cores"}
@@ -38,7 +38,7 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
            "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune",
-           "vie_solve_multi")
+           "vie_solve_multi", "vie_tucker_cp", "vie_cp_export")
 
 
 class VieError(RuntimeError):
@@ -59,7 +59,9 @@ class OpInfo(ctypes.Structure):
                 ("uncompressed_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("has_uncompressed", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int),
-                ("rebuild_kernel", ctypes.c_int)]
+                ("rebuild_kernel", ctypes.c_int), ("cp_rank", ctypes.c_int),
+                ("cp_rel_err", ctypes.c_double * 6), ("cp_sweeps", ctypes.c_int * 6),
+                ("cp_bytes", ctypes.c_size_t)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -98,6 +100,8 @@ def _load():
         "vie_matvec_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                              ctypes.POINTER(ci), ci, vp],
         "vie_autotune": [vp, ci, vp],
+        "vie_tucker_cp": [vp, ci, cd, ci, ctypes.c_ulonglong, vp],
+        "vie_cp_export": [vp, ci, pd, pd, pd, pd, ctypes.POINTER(ci), vp],
         "vie_solve_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                             ctypes.POINTER(vp), ctypes.POINTER(ci), ci, ci, ci,
                             ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
@@ -215,7 +219,9 @@ class Operator:
                 "workspace_bytes": inf.workspace_bytes,
                 "has_uncompressed": bool(inf.has_uncompressed), "max_batch": inf.max_batch,
                 "line_threads": tuple(inf.line_threads), "tuned_batch": inf.tuned_batch,
-                "rebuild_kernel": REBUILD_KERNELS[inf.rebuild_kernel]}
+                "rebuild_kernel": REBUILD_KERNELS[inf.rebuild_kernel],
+                "cp_rank": inf.cp_rank, "cp_rel_err": tuple(inf.cp_rel_err),
+                "cp_sweeps": tuple(inf.cp_sweeps), "cp_bytes": inf.cp_bytes}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""
@@ -229,6 +235,26 @@ class Operator:
         _check(lib.vie_op_export(self._h, c, dp(core), dp(U[0]), dp(U[1]), dp(U[2]),
                                  dp(S[0]), dp(S[1]), dp(S[2]), _stream()), "vie_op_export")
         return core, U, S
+
+    def tucker_cp(self, rank, tol=1e-9, max_iter=500, seed=0):
+        """Algorithm 2: CP-ALS with `rank` terms on each HOSVD core (vie_tucker_cp);
+        afterwards path="tucker_cp" applies eq. (17).  Returns the relative core
+        errors of the six components."""
+        _check(lib.vie_tucker_cp(self._h, int(rank), float(tol), int(max_iter), int(seed), _stream()),
+               "vie_tucker_cp")
+        return self.info()["cp_rel_err"]
+
+    def cp_export(self, c):
+        """([W1, W2, W3], rel_err, sweeps) of component c as complex128 numpy (all P_q rows)."""
+        inf = self.info()
+        R, P = inf["cp_rank"], inf["P"]
+        W = [np.zeros((P[q], R), dtype=np.complex128) for q in range(3)]
+        err = ctypes.c_double()
+        sw = ctypes.c_int()
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib.vie_cp_export(self._h, c, dp(W[0]), dp(W[1]), dp(W[2]), ctypes.byref(err),
+                                 ctypes.byref(sw), _stream()), "vie_cp_export")
+        return W, err.value, sw.value
 
     def reserve(self, max_batch):
         _check(lib.vie_reserve(self._h, int(max_batch)), "vie_reserve")

@@ -101,16 +101,31 @@ static int check_prec_path(int precision, int path, const vie_op* op) {
     set_error("precision must be VIE_C64 or VIE_C128");
     return VIE_ERR_ARG;
   }
-  if (path != VIE_PATH_TUCKER && path != VIE_PATH_UNCOMPRESSED) {
-    set_error("path must be VIE_PATH_TUCKER or VIE_PATH_UNCOMPRESSED");
+  if (path != VIE_PATH_TUCKER && path != VIE_PATH_UNCOMPRESSED && path != VIE_PATH_TUCKER_CP) {
+    set_error("path must be VIE_PATH_TUCKER, VIE_PATH_UNCOMPRESSED or VIE_PATH_TUCKER_CP");
     return VIE_ERR_ARG;
   }
   if (path == VIE_PATH_UNCOMPRESSED && op->spec32 == nullptr) {
     set_error("operator was built without VIE_STORE_UNCOMPRESSED");
     return VIE_ERR_ARG;
   }
+  if (path == VIE_PATH_TUCKER_CP && op->cp.R == 0) {
+    set_error("no Tucker+CP model: call vie_tucker_cp first");
+    return VIE_ERR_ARG;
+  }
   return VIE_OK;
 }
+
+// Operator applications with the Tucker+CP model exist in FP32 only.
+static int check_cp_precision(int precision, int path) {
+  if (path == VIE_PATH_TUCKER_CP && precision != VIE_C64) {
+    set_error("VIE_PATH_TUCKER_CP applies the FP32 model: use VIE_C64");
+    return VIE_ERR_ARG;
+  }
+  return VIE_OK;
+}
+
+void clear_error() { g_last_error.clear(); }
 
 #define CLEAR_ERROR() g_last_error.clear()
 
@@ -126,6 +141,7 @@ static int run_matvec(const vie_op* op, const void* in, void* out, int B, int pa
                       int pro, int epi, const void* chi, const void* addend, void* stream) {
   VIE_TRY(check_op(op, B));
   VIE_TRY(check_prec_path(precision, path, op));
+  VIE_TRY(check_cp_precision(precision, path));
   if (!in || !out) { set_error("NULL array"); return VIE_ERR_ARG; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == VIE_C64) return matvec_dispatch<float>(op, in, out, B, path, pro, epi, chi, addend, s);
@@ -183,6 +199,12 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   for (int i = 0; i < 4; ++i) r.line_threads[i] = op->tune.line_threads[i];
   r.tuned_batch = op->tune.tuned_batch;
   r.rebuild_kernel = op->oct32 == nullptr ? 0 : (octant_uses_tc(op) ? 2 : 1);
+  r.cp_rank = op->cp.R;
+  for (int c = 0; c < 6; ++c) {
+    r.cp_rel_err[c] = op->cp.err[c];
+    r.cp_sweeps[c] = op->cp.sweeps[c];
+  }
+  r.cp_bytes = op->cp.R == 0 ? 0 : (size_t)6 * (op->H[0] + op->H[1] + op->H[2]) * op->cp.R * sizeof(float2);
   *info = r;
   return VIE_OK;
 }
@@ -429,6 +451,7 @@ void vie_destroy(vie_op* op) {
   cudaFree(op->slab64);
   cudaFree(op->oct32);
   cudaFree(op->u3frag);
+  free_cp(op);
   cudaFree(op->spec32);
   cudaFree(op->spec64);
   for (int q = 0; q < 3; ++q) {

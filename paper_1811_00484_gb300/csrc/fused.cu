@@ -382,6 +382,56 @@ __global__ void u3frag_kernel(const CompMeta<float>* meta, int KS, int nsplit, i
   out[i] = v;
 }
 
+// GEMM 2 of one unit and its store: the 16 rows of G' for this CTA's n-tiles,
+// two n-tiles at a time, the hi*hi products and the two correction products
+// in separate accumulators (four independent chains).  C' columns 8 nt + 2 t
+// and + 1 are (Re, Im) of G[k2][4 nt + t].
+template <int KS>
+__device__ __forceinline__ void tc_gemm2_store(const uint32_t (&a2h)[KS][4], const uint32_t (&a2l)[KS][4],
+                                               const uint4* B2, int ntc, int nt_lo, int nt_n, int lane,
+                                               float2* o0, float2* o1, bool in0, bool in1, int H3) {
+  const int t = lane & 3;
+  for (int ntl = 0; ntl < nt_n; ntl += 2) {
+    float hh0[4] = {0.f, 0.f, 0.f, 0.f}, cr0[4] = {0.f, 0.f, 0.f, 0.f};
+    float hh1[4] = {0.f, 0.f, 0.f, 0.f}, cr1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < KS; ++j) {
+      const uint4 p = B2[(j * ntc + ntl) * 32 + lane];
+      const uint4 r = B2[(j * ntc + ntl + 1) * 32 + lane];
+      mma_tf32(cr0, a2l[j], p.x, p.y);
+      mma_tf32(cr1, a2l[j], r.x, r.y);
+      mma_tf32(cr0, a2h[j], p.z, p.w);
+      mma_tf32(cr1, a2h[j], r.z, r.w);
+      mma_tf32(hh0, a2h[j], p.x, p.y);
+      mma_tf32(hh1, a2h[j], r.x, r.y);
+    }
+    const int n0 = 4 * (nt_lo + ntl) + t, n1 = n0 + 4;
+    if (in0) {
+      if (n0 < H3) o0[n0] = make_float2(hh0[0] + cr0[0], hh0[1] + cr0[1]);
+      if (n1 < H3) o0[n1] = make_float2(hh1[0] + cr1[0], hh1[1] + cr1[1]);
+    }
+    if (in1) {
+      if (n0 < H3) o1[n0] = make_float2(hh0[2] + cr0[2], hh0[3] + cr0[3]);
+      if (n1 < H3) o1[n1] = make_float2(hh1[2] + cr1[2], hh1[3] + cr1[3]);
+    }
+  }
+}
+
+// One row of a partial k2 tile with FP32 FMAs: lane q holds w[q] (q < rq),
+// G[n] = sum_q w[q] F[n, q] for n in [nb, ne), F staged as [q][n - nb].
+__device__ __forceinline__ void fma_row(float2 w, int rq, const float2* Fs, int ncols, int nb, int ne,
+                                        float2* orow, int lane) {
+  for (int n0 = nb; n0 < ne; n0 += 32) {
+    const int n = n0 + lane;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < rq; ++q) {
+      const float2 wq = make_float2(__shfl_sync(0xffffffffu, w.x, q), __shfl_sync(0xffffffffu, w.y, q));
+      if (n < ne) acc = cmadd(wq, Fs[q * ncols + (n - nb)], acc);
+    }
+    if (n < ne) orow[n] = acc;
+  }
+}
+
 template <int KS>
 __global__ void __launch_bounds__(kTcThreads, 1) octant_tc_kernel(const OctTcArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -459,16 +509,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) octant_tc_kernel(const OctTcArg
         float2 w = make_float2(0.f, 0.f);
         if (lane < r3)
           for (int b = 0; b < r2; ++b) w = cmadd(u2[b], S[b * r3m + lane], w);
-        float2* orow = a.o.out + (((long long)k1l * H2 + k2) * 6 + c) * H3;
-        for (int n0 = nb; n0 < ne; n0 += 32) {
-          const int n = n0 + lane;
-          float2 acc = make_float2(0.f, 0.f);
-          for (int q = 0; q < r3; ++q) {
-            const float2 wq = make_float2(__shfl_sync(0xffffffffu, w.x, q), __shfl_sync(0xffffffffu, w.y, q));
-            if (n < ne) acc = cmadd(wq, U3s[q * ncols + (n - nb)], acc);
-          }
-          if (n < ne) orow[n] = acc;
-        }
+        fma_row(w, r3, U3s, ncols, nb, ne, a.o.out + (((long long)k1l * H2 + k2) * 6 + c) * H3, lane);
       }
       continue;
     }
@@ -505,39 +546,99 @@ __global__ void __launch_bounds__(kTcThreads, 1) octant_tc_kernel(const OctTcArg
       tf32_split(acc1[j][1], a2h[j][2], a2l[j][2]);
       tf32_split(acc1[j][3], a2h[j][3], a2l[j][3]);
     }
-    // GEMM 2: two n-tiles at a time, the hi*hi products and the two
-    // correction products in separate accumulators (four independent chains)
     float2* o0 = a.o.out + (((long long)k1l * H2 + row0) * 6 + c) * H3;
-    float2* o1 = o0 + 8ll * 6 * H3;
-    for (int ntl = 0; ntl < nt_n; ntl += 2) {
-      float hh0[4] = {0.f, 0.f, 0.f, 0.f}, cr0[4] = {0.f, 0.f, 0.f, 0.f};
-      float hh1[4] = {0.f, 0.f, 0.f, 0.f}, cr1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < KS; ++j) {
-        const uint4 p = B2[(j * a.ntc + ntl) * 32 + lane];
-        const uint4 r = B2[(j * a.ntc + ntl + 1) * 32 + lane];
-        mma_tf32(cr0, a2l[j], p.x, p.y);
-        mma_tf32(cr1, a2l[j], r.x, r.y);
-        mma_tf32(cr0, a2h[j], p.z, p.w);
-        mma_tf32(cr1, a2h[j], r.z, r.w);
-        mma_tf32(hh0, a2h[j], p.x, p.y);
-        mma_tf32(hh1, a2h[j], r.x, r.y);
-      }
-      // C' columns 8 nt + 2 t, + 1 are (Re, Im) of G[k2][4 nt + t]
-      const int n0 = 4 * (nt_lo + ntl) + t, n1 = n0 + 4;
-      if (row0 < H2) {
-        if (n0 < H3) o0[n0] = make_float2(hh0[0] + cr0[0], hh0[1] + cr0[1]);
-        if (n1 < H3) o0[n1] = make_float2(hh1[0] + cr1[0], hh1[1] + cr1[1]);
-      }
-      if (row1 < H2) {
-        if (n0 < H3) o1[n0] = make_float2(hh0[2] + cr0[2], hh0[3] + cr0[3]);
-        if (n1 < H3) o1[n1] = make_float2(hh1[2] + cr1[2], hh1[3] + cr1[3]);
-      }
-    }
+    tc_gemm2_store<KS>(a2h, a2l, B2, a.ntc, nt_lo, nt_n, lane, o0, o0 + 8ll * 6 * H3, row0 < H2,
+                       row1 < H2, H3);
   }
 }
 
-int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s);
+// Tucker+CP rebuild, eq. (17): G_c[k1, k2, k3] = sum_l W1[k1, l] W2[k2, l] W3[k3, l]
+// for the half fibres of a chunk of k1.  The same units and second GEMM as
+// octant_tc_kernel; the first GEMM becomes a Hadamard product: the A
+// fragments of a unit are A[k2][l] = W1[k1, l] W2[k2, l] (slot t of k-step j
+// is Re A[., 4 j + t], slot t + 4 its Im), and B is W3's real form in the same
+// fragment order (u3frag_kernel applied to W3).
+struct CpMeta {
+  const float2* W1;    // [H1][R]
+  const float2* W2;    // [H2][R]
+  const float2* W3t;   // [R][H3]
+};
+
+struct OctCpArgs {
+  const CpMeta* meta;
+  const uint4* frag;   // [6][nsplit][KS][ntc][32]
+  float2* out;         // [chunk][H2][6][H3]
+  int R, H2, H3, k1a, nk1, mt, nt2, nsplit, ntc, per, kspan;
+};
+
+template <int KS>
+__global__ void __launch_bounds__(kTcThreads, 1) octant_cp_kernel(const OctCpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.x / a.nsplit, sp = blockIdx.x - c * a.nsplit;
+  const CpMeta m = a.meta[c];
+  const int H2 = a.H2, H3 = a.H3, R = a.R;
+  const int units = a.nk1 * a.mt;
+  const int u0 = blockIdx.y * a.per, u1 = min(units, u0 + a.per);
+  if (u0 >= u1) return;
+  const int k1lo = u0 / a.mt, kspan = (u1 - 1) / a.mt - k1lo + 1;
+  const int rows = a.mt * 16, ncols = 4 * a.ntc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int nt_lo = sp * a.ntc, nt_n = min(a.ntc, a.nt2 - nt_lo);
+  uint4* B2 = reinterpret_cast<uint4*>(smem_raw);                 // [KS][ntc][32]
+  float2* W2s = reinterpret_cast<float2*>(B2 + KS * a.ntc * 32);  // [mt 16][R]
+  float2* W1s = W2s + rows * R;                                   // [kspan][R]
+  float2* W3s = W1s + a.kspan * R;                                // [R][4 ntc]: W3[n0 + i, l]
+  {
+    const uint4* fr = a.frag + ((long long)c * a.nsplit + sp) * KS * a.ntc * 32;
+    for (int i = threadIdx.x; i < KS * a.ntc * 32; i += kTcThreads) cp_async16(B2 + i, fr + i);
+    for (int i = threadIdx.x; i < rows * R; i += kTcThreads) {
+      if (i < H2 * R) cp_async8(W2s + i, m.W2 + i);
+      else W2s[i] = make_float2(0.f, 0.f);
+    }
+    const float2* w1 = m.W1 + (long long)(a.k1a + k1lo) * R;
+    for (int i = threadIdx.x; i < kspan * R; i += kTcThreads) cp_async8(W1s + i, w1 + i);
+    for (int i = threadIdx.x; i < R * ncols; i += kTcThreads) {
+      const int l = i / ncols, n = 4 * nt_lo + (i - l * ncols);
+      if (n < H3) cp_async8(W3s + i, m.W3t + (long long)l * H3 + n);
+      else W3s[i] = make_float2(0.f, 0.f);
+    }
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const int rem = H2 - 16 * (H2 / 16);
+  for (int u = u0 + warp; u < u1; u += kTcWarps) {
+    const int k1l = u / a.mt, mt = u - k1l * a.mt;
+    const float2* w1 = W1s + (k1l - k1lo) * R;
+    if (rem > 0 && rem <= kTcSimtRows && mt == a.mt - 1) {
+      const int nb = 4 * nt_lo, ne = min(H3, 4 * (nt_lo + nt_n));
+      for (int k2 = 16 * mt; k2 < H2; ++k2) {
+        const float2 w = lane < R ? w1[lane] * W2s[k2 * R + lane] : make_float2(0.f, 0.f);
+        fma_row(w, R, W3s, ncols, nb, ne, a.out + (((long long)k1l * H2 + k2) * 6 + c) * H3, lane);
+      }
+      continue;
+    }
+    const int row0 = mt * 16 + g, row1 = row0 + 8;
+    uint32_t a2h[KS][4], a2l[KS][4];
+#pragma unroll
+    for (int j = 0; j < KS; ++j) {
+      const int l = 4 * j + t;
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      if (l < R) {
+        v0 = w1[l] * W2s[row0 * R + l];
+        v1 = w1[l] * W2s[row1 * R + l];
+      }
+      tf32_split(v0.x, a2h[j][0], a2l[j][0]);
+      tf32_split(v1.x, a2h[j][1], a2l[j][1]);
+      tf32_split(v0.y, a2h[j][2], a2l[j][2]);
+      tf32_split(v1.y, a2h[j][3], a2l[j][3]);
+    }
+    float2* o0 = a.out + (((long long)k1l * H2 + row0) * 6 + c) * H3;
+    tc_gemm2_store<KS>(a2h, a2l, B2, a.ntc, nt_lo, nt_n, lane, o0, o0 + 8ll * 6 * H3, row0 < H2,
+                       row1 < H2, H3);
+  }
+}
+
+int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s, bool cp);
 
 // Four-step variant (fused_fs_group) for P3 = 8 V, V = 4 R with R even.
 __host__ __device__ constexpr int fused_fs_min_blocks(int V) { return V <= 8 ? 8 : (V <= 16 ? 5 : 4); }
@@ -577,7 +678,7 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   const int chunk = a.oct_chunk;
   for (int k1a = 0; k1a < a.H1; k1a += chunk) {
     const int nk1 = std::min(chunk, a.H1 - k1a);
-    if (k1a > 0 || !a.oct_first_ready) launch_octant_args(a.op, k1a, s);
+    if (k1a > 0 || !a.oct_first_ready) launch_octant_args(a.op, k1a, s, a.oct_cp);
     a.oct_k1a = k1a;
     a.g0 = k1a * a.H2;
     ProfScope ps(fam, s);
@@ -715,8 +816,8 @@ vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool sto
   return a;
 }
 
-int launch_octant(const vie_op* op, int k1a, cudaStream_t s) {
-  return vie::launch_octant_args(op, k1a, s);
+int launch_octant(const vie_op* op, int k1a, cudaStream_t s, bool cp) {
+  return vie::launch_octant_args(op, k1a, s, cp);
 }
 
 bool octant_uses_tc(const vie_op* op) { return op->u3frag != nullptr; }
@@ -774,12 +875,61 @@ static OctArgs octant_args(const vie_op* op, int k1a) {
   return o;
 }
 
-// the rebuild of chunk [k1a, k1a + oct_k1): tensor cores when the operator
-// holds the U3 fragments (r3 <= 32 and no VIE_REBUILD_SIMT), else FMAs
-int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s) {
+template <int KS>
+static void launch_cp(const OctCpArgs& t, int gy, size_t smem, cudaStream_t s) {
+  octant_cp_kernel<KS><<<dim3(6 * t.nsplit, gy), kTcThreads, smem, s>>>(t);
+}
+
+// launch shape of octant_cp_kernel for nk1 values of k1; returns its shared memory
+static size_t cp_plan(const vie_op* op, int k1a, int nk1, OctCpArgs* t) {
+  t->meta = reinterpret_cast<const CpMeta*>(op->cp.meta);
+  t->frag = op->cp.frag;
+  t->out = op->oct32;
+  t->R = op->cp.R;
+  t->H2 = op->H[1];
+  t->H3 = op->H[2];
+  t->k1a = k1a;
+  t->nk1 = nk1;
+  t->mt = (t->H2 + 15) / 16;
+  t->nt2 = (t->H3 + 3) / 4;
+  t->nsplit = op->cp.nsplit;
+  t->ntc = op->cp.ntc;
+  const int units = nk1 * t->mt;
+  int gy = std::max(1, std::min(units, device_sms() / (6 * t->nsplit)));
+  for (;;) {
+    t->per = (units + gy - 1) / gy;
+    t->kspan = (t->per + t->mt - 1) / t->mt + 1;
+    const size_t smem = (size_t)op->cp.ks * t->ntc * 32 * sizeof(uint4) +
+                        ((size_t)t->mt * 16 + t->kspan + 4 * t->ntc) * t->R * sizeof(float2);
+    if (smem <= kTcSmemLimit || t->per == 1) return smem;
+    gy = std::min(units, 2 * gy);
+  }
+}
+
+// the rebuild of chunk [k1a, k1a + oct_k1): from the Tucker+CP model (cp), or
+// from the Tucker model on the tensor cores when the operator holds the U3
+// fragments (r3 <= 32 and no VIE_REBUILD_SIMT), else with FMAs
+int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s, bool cp) {
   const OctArgs o = octant_args(op, k1a);
   const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
   ProfScope ps(PF_REBUILD, s);
+  if (cp) {
+    OctCpArgs t;
+    const size_t smem = cp_plan(op, k1a, nk1, &t);
+    const int gy = (nk1 * t.mt + t.per - 1) / t.per;
+    switch (op->cp.ks) {
+      case 1: launch_cp<1>(t, gy, smem, s); break;
+      case 2: launch_cp<2>(t, gy, smem, s); break;
+      case 3: launch_cp<3>(t, gy, smem, s); break;
+      case 4: launch_cp<4>(t, gy, smem, s); break;
+      case 5: launch_cp<5>(t, gy, smem, s); break;
+      case 6: launch_cp<6>(t, gy, smem, s); break;
+      case 7: launch_cp<7>(t, gy, smem, s); break;
+      default: launch_cp<8>(t, gy, smem, s); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VIE_OK : cuda_status(e, "Tucker+CP rebuild launch");
+  }
   OctTcArgs t;
   const size_t smem = op->u3frag != nullptr ? tc_plan(op, o, nk1, &t) : 0;
   if (op->u3frag != nullptr && smem <= kTcSmemLimit) {
@@ -824,10 +974,52 @@ int launch_u3_fragments(const vie_op* op, cudaStream_t s) {
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "U3 fragment launch");
 }
 
+// Operands of the Tucker+CP rebuild once the factors W^q exist: W3's real form
+// in fragment order (u3frag_kernel reads W3 through a CompMeta whose U3t and
+// r3 are W3t and R) and the per-component pointer records.
+int build_cp_rebuild(vie_op* op, cudaStream_t s) {
+  const int R = op->cp.R;
+  tc_layout(R, op->H[2], &op->cp.ks, &op->cp.nsplit, &op->cp.ntc);
+  CompMeta<float> m[6] = {};
+  vie::CpMeta cm[6];
+  for (int c = 0; c < 6; ++c) {
+    m[c].U3t = op->cp.W3t32[c];
+    m[c].r3 = R;
+    cm[c] = vie::CpMeta{op->cp.W32[c][0], op->cp.W32[c][1], op->cp.W3t32[c]};
+  }
+  const size_t nfrag = 6ull * op->cp.nsplit * op->cp.ks * op->cp.ntc * 32;
+  CompMeta<float>* dm = nullptr;
+  cudaError_t e = cudaMalloc(&op->cp.frag, nfrag * sizeof(uint4));
+  if (e == cudaSuccess) e = cudaMalloc(&op->cp.meta, sizeof(cm));
+  if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(m));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dm);
+    set_error("out of device memory for the Tucker+CP rebuild operands");
+    return VIE_ERR_OOM;
+  }
+  e = cudaMemcpy(op->cp.meta, cm, sizeof(cm), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dm, m, sizeof(m), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    vie::u3frag_kernel<<<(unsigned)((nfrag + 255) / 256), 256, 0, s>>>(dm, op->cp.ks, op->cp.nsplit,
+                                                                      op->cp.ntc, op->H[2], op->cp.frag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dm);
+  if (e != cudaSuccess) return cuda_status(e, "Tucker+CP rebuild operands");
+  vie::OctCpArgs t;
+  if (vie::cp_plan(op, 0, op->oct_k1, &t) > vie::kTcSmemLimit) {
+    set_error("the Tucker+CP rebuild of rank %d does not fit in shared memory", R);
+    return VIE_ERR_ARG;
+  }
+  return VIE_OK;
+}
+
 
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
-                 cudaStream_t s, bool first_chunk_ready) {
+                 cudaStream_t s, bool first_chunk_ready, bool cp) {
   vie::FusedArgs<T> a = make_fused_args<T>(op, data, B, stored, active);
   if constexpr (sizeof(T) == 4) {
     if (!stored && op->oct32 != nullptr) {
@@ -835,6 +1027,7 @@ int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* a
       a.oct_chunk = op->oct_k1;
       a.op = op;
       a.oct_first_ready = first_chunk_ready;
+      a.oct_cp = cp;
     }
   }
   if (stored) {
@@ -868,6 +1061,14 @@ int fused_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_cp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   // octant_kernel also holds the six metadata records in static shared memory
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::octant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "fused kernel attributes");
@@ -877,5 +1078,5 @@ template vie::SlabArgs<float> make_slab_args<float>(const vie_op*);
 template vie::FusedArgs<float> make_fused_args<float>(const vie_op*, float2*, int, bool, const int*);
 template int launch_slab_cores<float>(const vie_op*, cudaStream_t);
 template int launch_slab_cores<double>(const vie_op*, cudaStream_t);
-template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t, bool);
-template int launch_fused<double>(const vie_op*, double2*, int, bool, const int*, cudaStream_t, bool);
+template int launch_fused<float>(const vie_op*, float2*, int, bool, const int*, cudaStream_t, bool, bool);
+template int launch_fused<double>(const vie_op*, double2*, int, bool, const int*, cudaStream_t, bool, bool);

@@ -15,7 +15,7 @@
 
 template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
-                 cudaStream_t s, bool first_chunk_ready);
+                 cudaStream_t s, bool first_chunk_ready, bool cp);
 
 size_t workspace_bytes_for(const vie_op* op, int B) {
   const size_t n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
@@ -159,13 +159,15 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
 
 // Rebuild the scratch for the next FP32 Tucker matvec on the side stream, ordered
 // after the work already on s (the fused kernel that last read the scratch).
-int prefetch_rebuild(const vie_op* op, cudaStream_t s) {
+int prefetch_rebuild(const vie_op* op, cudaStream_t s, bool cp) {
   if (op->oct32 == nullptr || op->rb_stream == nullptr) return VIE_OK;
   VIE_CUDA(cudaEventRecord(op->rb_fork, s));
   VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
-  VIE_TRY(launch_octant(op, 0, op->rb_stream));
+  VIE_TRY(launch_octant(op, 0, op->rb_stream, cp));
   VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
-  const_cast<vie_op*>(op)->rb_pending = true;
+  vie_op* opm = const_cast<vie_op*>(op);
+  opm->rb_pending = true;
+  opm->rb_cp = cp;
   return VIE_OK;
 }
 
@@ -177,6 +179,7 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
                int mv_flags) {
   using C = cx<T>;
   const bool stored = (path == VIE_PATH_UNCOMPRESSED);
+  const bool cp = (path == VIE_PATH_TUCKER_CP);
   const LineStages<T> st = make_line_stages<T>(op, ws, in, out, B, pro_flags, epi_flags, chi,
                                                addend, active, rscale, rscale_stride);
   C* T2 = const_cast<C*>(st.s[1].out);
@@ -188,10 +191,11 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   bool pre = false;
   const bool side = !stored && op->oct32 != nullptr && op->rb_stream != nullptr;
   if constexpr (sizeof(T) == 4) {
-    if (side && !op->rb_pending) {
+    // a pending rebuild of the other model is overwritten (same stream, in order)
+    if (side && !(op->rb_pending && op->rb_cp == cp)) {
       VIE_CUDA(cudaEventRecord(op->rb_fork, s));
       VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
-      VIE_TRY(launch_octant(op, 0, op->rb_stream));
+      VIE_TRY(launch_octant(op, 0, op->rb_stream, cp));
       VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
     }
     pre = side;
@@ -200,10 +204,10 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
   launch_line_fft<T>(st.s[0], s);
   launch_line_fft<T>(st.s[1], s);
   if (pre) VIE_CUDA(cudaStreamWaitEvent(s, op->rb_join, 0));
-  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s, pre));
+  VIE_TRY(launch_fused<T>(op, T2, B, stored, active, s, pre, cp));
   launch_line_fft<T>(st.s[2], s);
   launch_line_fft<T>(st.s[3], s);
-  if (pre && (mv_flags & MV_PREFETCH_REBUILD)) VIE_TRY(prefetch_rebuild(op, s));
+  if (pre && (mv_flags & MV_PREFETCH_REBUILD)) VIE_TRY(prefetch_rebuild(op, s, cp));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "matvec launch");
   return VIE_OK;

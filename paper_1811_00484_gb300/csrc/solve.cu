@@ -673,6 +673,7 @@ struct SolverState {
   int graph_adjoint = -1;
   int graph_prof = -1;                        // profiler epoch the graph was captured in
   int graph_passes = -1;                      // Gram-Schmidt passes baked into the graph
+  unsigned graph_cp_epoch = ~0u;              // Tucker+CP model the graph's rebuilds read
   std::vector<ProfEventPair> graph_events;    // event nodes of the captured graph
   bool graph_pending = false;                 // a replay ran since the last harvest
 };
@@ -867,7 +868,8 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
                  prof_bytes(PF_DOTS), (k + 2) * vec);
     }
     // the next matvec's rebuild, beside the rest of this step's Gram-Schmidt work
-    if (pass == 0 && path == VIE_PATH_TUCKER) VIE_TRY(prefetch_rebuild(op, s));
+    if (pass == 0 && (path == VIE_PATH_TUCKER || path == VIE_PATH_TUCKER_CP))
+      VIE_TRY(prefetch_rebuild(op, s, path == VIE_PATH_TUCKER_CP));
     {
       ProfScope ps(PF_SMALL, s);
       launch_pdl(reduce_dots_kernel, dim3(k + 1, B), dim3(kReduceThreads), 0, s,
@@ -941,7 +943,8 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
   // the graph bakes in every pointer it touches: rebuild it when any changes
   if (st->exec && (st->graph_chi != chi || st->graph_stream != s || st->path != path ||
                    st->graph_adjoint != adjoint || st->graph_ws != op->ws.ptr ||
-                   st->graph_prof != prof_epoch() || st->graph_passes != passes)) {
+                   st->graph_prof != prof_epoch() || st->graph_passes != passes ||
+                   st->graph_cp_epoch != op->cp.epoch)) {
     drop_graph(st);
   }
   if (!st->exec) {
@@ -972,6 +975,7 @@ static int run_cycle(const vie_op* op, SolverState* st, const float2* chi, int p
     st->graph_ws = op->ws.ptr;
     st->graph_prof = prof_epoch();
     st->graph_passes = passes;
+    st->graph_cp_epoch = op->cp.epoch;
   }
   VIE_CUDA(cudaGraphLaunch(st->exec, s));
   st->graph_pending = true;
@@ -1061,6 +1065,8 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
                     int flags, int precision, const vie_solve_opts* o, vie_solve_info* info,
                     cudaStream_t s) {
   const int path = o->path;
+  // Tucker+CP is an FP32 model: FP64 residuals use the Tucker model it approximates
+  const int path64 = path == VIE_PATH_TUCKER_CP ? VIE_PATH_TUCKER : path;
   const int adjoint = (flags & VIE_SOLVE_ADJOINT) ? 1 : 0;
   const long long nvox = (long long)op->n[0] * op->n[1] * op->n[2];
   const long long N = st->N, total = N * B;
@@ -1081,10 +1087,10 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
   for (;; ++step) {
     if (have_x) {
       if (!adjoint)
-        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path, 0, EPI_SUB | EPI_CHI, st->chi64, st->x,
+        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path64, 0, EPI_SUB | EPI_CHI, st->chi64, st->x,
                                     nullptr, s));
       else
-        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB,
+        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path64, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB,
                                     st->chi64, st->x, nullptr, s));
       mv64 += B;
     }

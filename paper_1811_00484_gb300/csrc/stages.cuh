@@ -43,6 +43,7 @@ template <typename T> struct FusedArgs {
   int oct_chunk;               // k1 values per fill of `octant`
   bool oct_first_ready;        // host: chunk 0 already rebuilt on the side stream (joined)
   const vie_op* op;            // host: the operator (rebuild launches of later chunks)
+  bool oct_cp;                 // host: rebuild from the Tucker+CP model (eq. (17))
   int g0;                      // group of the first CTA (k1 chunks)
   int lines_per_round;         // z-lines (x3 components) held in shared memory at once
   int ld;                      // shared-memory line stride

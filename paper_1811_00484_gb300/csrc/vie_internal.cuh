@@ -179,6 +179,23 @@ struct Tuning {
   int tuned_batch = 0;                          // batch the choice was timed at (0 = default)
 };
 
+// Tucker+CP model (Algorithm 2, eq. (17)), formed by vie_tucker_cp: factors
+// W^q = U^q V^q for the stored half rows ([H_q][R]; rows P_q - k follow by the
+// parity sign of U^q), and the operands of the per-matvec rebuild.
+constexpr int kCpMaxRank = 32;
+struct CpModel {
+  int R = 0;                               // 0: no model
+  double err[6] = {};                      // relative core error ||G - CP|| / ||G||
+  int sweeps[6] = {};
+  double2* W64[6][3] = {};
+  float2* W32[6][3] = {};
+  float2* W3t32[6] = {};                   // W3 transposed [R][H3]
+  void* meta = nullptr;                    // device records of the rebuild kernel
+  uint4* frag = nullptr;                   // W3 in fragment order [6][nsplit][ks][ntc][32]
+  int ks = 0, nsplit = 0, ntc = 0;
+  unsigned epoch = 0;                      // bumped whenever the model's buffers change
+};
+
 struct vie_op {
   vie_grid grid;
   int n[3], P[3], H[3];
@@ -200,10 +217,12 @@ struct vie_op {
   // host-side, in launch order: chunk 0 of the next matvec's rebuild is already
   // enqueued on rb_stream (started by the previous matvec, see MV_PREFETCH_REBUILD)
   bool rb_pending = false;
+  bool rb_cp = false;        // the pending (or last) rebuild used the Tucker+CP model
   // tensor-core rebuild: the real form of U3^T, split into TF32 value and
   // remainder, in mma fragment order [6][tc_nsplit][tc_ks][tc_ntc][32]
   uint4* u3frag = nullptr;
   int tc_ks = 0, tc_nsplit = 0, tc_ntc = 0;
+  CpModel cp;
   // stored spectra (optional)
   float2* spec32 = nullptr;  double2* spec64 = nullptr;
   FftPlan plan[3];
@@ -232,6 +251,7 @@ template <typename T> struct CompMeta {
 // helpers
 // ---------------------------------------------------------------------------
 void set_error(const char* fmt, ...);
+void clear_error();
 int cuda_status(cudaError_t e, const char* what);
 #define VIE_CUDA(call)                                          \
   do {                                                          \
@@ -255,7 +275,7 @@ double wavenumber(double freq_hz);
 // next matvec joins it); the caller must make another Tucker matvec follow
 enum { MV_PREFETCH_REBUILD = 1 };
 // start that rebuild now (after the work already on s); the next matvec joins it
-int prefetch_rebuild(const vie_op* op, cudaStream_t s);
+int prefetch_rebuild(const vie_op* op, cudaStream_t s, bool cp = false);
 template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
@@ -289,7 +309,7 @@ constexpr size_t kOctantSmemMax = 200u << 10;
 __host__ __device__ constexpr size_t octant_smem_bytes(int r2max, int r3max) {
   return (size_t)(6 * r3max * kOctantK2 + 6 * r2max * r3max + 6 * kOctantK2 * r2max) * sizeof(float2);
 }
-int launch_octant(const vie_op* op, int k1a, cudaStream_t s);
+int launch_octant(const vie_op* op, int k1a, cudaStream_t s, bool cp = false);
 // the rebuild runs on the tensor cores (octant_tc_kernel, when the operator
 // holds the U3 fragments), else on the FP32-FMA octant_kernel
 bool octant_uses_tc(const vie_op* op);
@@ -297,6 +317,8 @@ bool tc_rebuild_eligible(const vie_op* op);
 void tc_layout(int r3max, int H3, int* ks, int* nsplit, int* ntc);
 bool tc_rebuild_fits(const vie_op* op);
 int launch_u3_fragments(const vie_op* op, cudaStream_t s);
+int build_cp_rebuild(vie_op* op, cudaStream_t s);
+void free_cp(vie_op* op);
 
 // setup internals (setup.cu)
 int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, cudaStream_t s,
