@@ -39,6 +39,7 @@ def parse():
     p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
+    p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
     p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1"],
                    help="matvec: only K timed batched matvecs; solve1: K solves only "
                         "(small commands for profilers)")
@@ -470,6 +471,27 @@ def main():
     matvec_rate("tucker", reps=10)
     kern_mv = vie.profile_stop()
 
+    # Tucker+CP (Algorithm 2) on the same operator, after the headline runs: CP-ALS
+    # with 32 terms on each core, then isolated matvecs and one solve on that path
+    # (its inner FP32 GMRES applies eq. (17); FP64 refinement residuals the Tucker model)
+    tucker_cp = None
+    if not args.no_cp:
+        barrier()
+        t0 = time.perf_counter()
+        cp_err = op.tucker_cp(32, tol=1e-10, max_iter=300, seed=0)
+        barrier()
+        t_als = time.perf_counter() - t0
+        mv_rate_cp, mv_ms_cp = matvec_rate("tucker_cp")
+        op.solve(chi, einc, path="tucker_cp", **solve_kw)
+        t_cp, mv_cp, it_cp = timed_solves("tucker_cp", 1)
+        icp = op.info()
+        tucker_cp = {"rank": 32, "als_ms": 1e3 * t_als, "als_sweeps": list(icp["cp_sweeps"]),
+                     "core_rel_err_max": max(cp_err), "cp_bytes": icp["cp_bytes"],
+                     "matvec_ms": mv_ms_cp, "matvecs_per_s": mv_rate_cp,
+                     "solve_ms": 1e3 * t_cp, "solve_matvecs": mv_cp,
+                     "iterations": it_cp[-1]["iterations"], "refine_steps": it_cp[-1]["refine_steps"],
+                     "relres": it_cp[-1]["relres"]}
+
     # the batched workload: 96^3 (192^3 padded), 16 ring-dipole right-hand sides in one
     # solve, HOSVD 1e-6; one warm-up and one timed solve, no instrumentation
     batched = None
@@ -559,6 +581,7 @@ def main():
                    "slab_bytes": info["slab_bytes"],
                    "rebuild_scratch_bytes": info["rebuild_scratch_bytes"], "ranks": info["ranks"]},
         "batched": batched,
+        "tucker_cp": tucker_cp,
         "clocks": clocks,
         "e2e": {"value": mv_e2e_all / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": chi_h.numel() * 8 + einc_h.numel() * 8,
