@@ -40,9 +40,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
-    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1"],
+    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1", "ranks"],
                    help="matvec: only K timed batched matvecs; solve1: K solves only "
-                        "(small commands for profilers)")
+                        "(small commands for profilers); ranks: the multilinear rank of "
+                        "the Green's tensors against frequency (Sec. VI.A, Fig. 4)")
+    p.add_argument("--max-n", type=int, default=300, help="ranks: largest grid edge built")
     p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
     p.add_argument("--orth", type=int, default=1, choices=[1, 2],
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
@@ -329,6 +331,52 @@ def run_matvec_mode(args):
                       "ms_per_matvec_batch": ms, "matvecs_per_s": args.batch / (ms * 1e-3)}))
 
 
+def smooth7(n):
+    """The 7-smooth integer nearest to n (the padded edge 2 n must factor into 2, 3, 5, 7)."""
+    def ok(v):
+        for p in (2, 3, 5, 7):
+            while v % p == 0:
+                v //= p
+        return v == 1
+    for d in range(0, n):
+        for v in (n - d, n + d):
+            if v >= 1 and ok(v):
+                return v
+    return 1
+
+
+def run_ranks_mode(args):
+    """Maximum Tucker rank over the six components against frequency, for a cube
+    of unit edge at resolutions lambda/10, lambda/20, lambda/30 and HOSVD tolerance
+    1e-8, f = 0.3 i GHz, i = 1..10: the sweep of Sec. VI.A (Fig. 4), with the
+    point-collocated dyadic kernel in place of the paper's PWL components.  The
+    edge n is the 7-smooth integer nearest to (cube edge) / (lambda / m); h = 1/n,
+    so the cube stays exactly 1 m and the resolution is reported as lambda / h."""
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+
+    c0 = 299792458.0
+    for per in (10, 20, 30):
+        for i in range(1, 11):
+            f = 0.3e9 * i
+            lam = c0 / f
+            n = smooth7(max(2, round(per / lam)))
+            if n > args.max_n:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op = vie.Operator((n, n, n), 1.0 / n, f, 1e-8)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ranks = op.info()["ranks"]
+            op.close()
+            print(json.dumps({"mode": "ranks", "f_ghz": round(f / 1e9, 3), "per_lambda": per,
+                              "n": n, "lambda_over_h": round(lam * n, 2), "tol": 1e-8,
+                              "max_rank": max(max(r) for r in ranks), "ranks": ranks,
+                              "setup_s": round(dt, 3)}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
@@ -342,6 +390,8 @@ def main():
         return run_matvec_mode(args)
     if args.mode == "solve1":
         return run_solve1_mode(args)
+    if args.mode == "ranks":
+        return run_ranks_mode(args)
     import numpy as np
     import torch
 
