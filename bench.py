@@ -40,10 +40,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
-    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1", "ranks"],
+    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1", "ranks", "tolerance"],
                    help="matvec: only K timed batched matvecs; solve1: K solves only "
                         "(small commands for profilers); ranks: the multilinear rank of "
-                        "the Green's tensors against frequency (Sec. VI.A, Fig. 4)")
+                        "the Green's tensors against frequency (Sec. VI.A, Fig. 4); tolerance: "
+                        "operator error against the HOSVD tolerance (Sec. VI.C, Fig. 7)")
     p.add_argument("--max-n", type=int, default=300, help="ranks: largest grid edge built")
     p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
     p.add_argument("--orth", type=int, default=1, choices=[1, 2],
@@ -377,6 +378,39 @@ def run_ranks_mode(args):
                               "setup_s": round(dt, 3)}), flush=True)
 
 
+def run_tolerance_mode(args):
+    """Operator error against the HOSVD tolerance on the bench workload (Sec. VI.C,
+    Fig. 7): for each tol, the FP64 Tucker matvec and the FP32 Tucker+CP matvec
+    (32 terms, 300 ALS sweeps) against the FP64 matvec with the stored
+    uncompressed spectra, relative L2 over one random field."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    wl = workloads.make("tolerance", args.n, seed=1, tol_svd=1e-6)
+    J64 = torch.from_numpy(wl.J).to(torch.complex128).cuda()
+    ref = None
+    for e in range(2, 10):
+        tol = 10.0 ** (-e)
+        op = vie.Operator(wl.n, wl.h, wl.freq_hz, tol, store_uncompressed=ref is None)
+        if ref is None:
+            ref = op.matvec(J64, path="uncompressed")
+        nref = torch.linalg.vector_norm(ref).item()
+        err_t = torch.linalg.vector_norm(op.matvec(J64) - ref).item() / nref
+        cp_err = op.tucker_cp(32, tol=1e-10, max_iter=300, seed=0)
+        y_cp = op.matvec(J64.to(torch.complex64), path="tucker_cp").to(torch.complex128)
+        err_cp = torch.linalg.vector_norm(y_cp - ref).item() / nref
+        inf = op.info()
+        print(json.dumps({"mode": "tolerance", "n": args.n, "tol": tol,
+                          "max_rank": max(max(r) for r in inf["ranks"]),
+                          "tucker_bytes": inf["tucker_bytes"], "tucker_matvec_rel_err": err_t,
+                          "cp_rank": 32, "cp_core_rel_err_max": max(cp_err),
+                          "cp_matvec_rel_err": err_cp}), flush=True)
+        op.close()
+
+
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
@@ -392,6 +426,8 @@ def main():
         return run_solve1_mode(args)
     if args.mode == "ranks":
         return run_ranks_mode(args)
+    if args.mode == "tolerance":
+        return run_tolerance_mode(args)
     import numpy as np
     import torch
 
