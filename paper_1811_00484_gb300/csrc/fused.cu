@@ -11,12 +11,13 @@
 // fibres k3 <= P3/2 of the octant k1 <= P1/2, k2 <= P2/2 are rebuilt, and
 // each serves, with signs, the up-to-four z-lines (k1 | P1-k1, k2 | P2-k2)
 // of every right-hand side.  On the register path the half fibres of a chunk
-// of k1 are rebuilt by octant_kernel into an FP32 scratch (one k1 chunk at a
-// time, so the scratch stays a small fraction of the uncompressed spectra),
-// and one CTA per (k1, k2) mirror group copies its 6 x (P3/2 + 1) values to
-// shared memory; the multi-grid and shared-memory variants rebuild the fibre
-// in the CTA.  The stored (uncompressed) variant reads the six spectra from
-// memory instead.
+// of k1 are rebuilt into an FP32 scratch (one k1 chunk at a time, so the
+// scratch stays a small fraction of the uncompressed spectra) by
+// octant_tc_kernel on the tensor cores (or octant_kernel with FP32 FMAs, or,
+// for the Tucker+CP model of eq. (17), octant_cp_kernel), and one CTA per
+// (k1, k2) mirror group copies its 6 x (P3/2 + 1) values to shared memory;
+// the multi-grid and shared-memory variants rebuild the fibre in the CTA.
+// The stored (uncompressed) variant reads the six spectra from memory instead.
 #include <algorithm>
 
 #include "stages.cuh"

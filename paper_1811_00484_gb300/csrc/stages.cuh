@@ -503,7 +503,7 @@ __device__ __forceinline__ void fused_warp_group(const FusedArgs<float>& a, int 
   };
   if (has_line && b0 < a.B) load_lines(b0);
   if (!STORED && !rebuild_here) {
-    // the group's half fibres, rebuilt for this matvec by octant_kernel
+    // the group's half fibres, rebuilt for this matvec into the scratch
     const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
     for (int it = tid; it < 6 * H3; it += nth) {
       const int c = it / H3, kk = it - c * H3;
@@ -620,7 +620,7 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
     atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
   }
   if (!STORED) {
-    // the group's half fibres, rebuilt for this matvec by octant_kernel
+    // the group's half fibres, rebuilt for this matvec into the scratch
     const C* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * H3;
     for (int it = tid; it < 6 * H3; it += nth) {
       const int c = it / H3, kk = it - c * H3;
