@@ -261,8 +261,9 @@ static int tucker_cp_impl(vie_op* op, int R, double tol, int max_iter, unsigned 
                   op->comp[c].r[q], kMaxTucker, c, kMaxTucker);
         return VIE_ERR_ARG;
       }
+  // work of any stream may still read the model being replaced
+  VIE_CUDA(cudaDeviceSynchronize());
   free_cp(op);
-  VIE_CUDA(cudaStreamSynchronize(s));
   // ALS
   AlsArgs a;
   for (int c = 0; c < 6; ++c) {
@@ -276,9 +277,14 @@ static int tucker_cp_impl(vie_op* op, int R, double tol, int max_iter, unsigned 
   double2* V = nullptr;
   double* err = nullptr;
   int* sweeps = nullptr;
-  VIE_TRY(cp_alloc(&V, (size_t)6 * 3 * kMaxTucker * R * sizeof(double2)));
-  VIE_TRY(cp_alloc(&err, 6 * sizeof(double)));
-  VIE_TRY(cp_alloc(&sweeps, 6 * sizeof(int)));
+  int arc = cp_alloc(&V, (size_t)6 * 3 * kMaxTucker * R * sizeof(double2));
+  if (arc == VIE_OK) arc = cp_alloc(&err, 6 * sizeof(double));
+  if (arc == VIE_OK) arc = cp_alloc(&sweeps, 6 * sizeof(int));
+  if (arc != VIE_OK) {
+    cudaFree(V);
+    cudaFree(err);
+    return arc;
+  }
   VIE_CUDA(cudaMemsetAsync(V, 0, (size_t)6 * 3 * kMaxTucker * R * sizeof(double2), s));
   a.V = V;
   a.err = err;
