@@ -78,3 +78,44 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(vie.Grid) == 3 * 4 + 4 + 2 * 8
     assert ctypes.sizeof(vie.SolveOpts) == 8 + 4 + 4 + 8 + 5 * 4 + 4   # trailing pad to 8
     assert ctypes.sizeof(vie.SolveInfo) == 4 * 4 + 8 + 65 * 8
+
+
+def test_struct_offsets_match_a_c_compile_of_the_header(tmp_path):
+    """Every field offset of the ctypes mirrors equals offsetof() in a C program
+    compiled against include/vie.h (gcc), so a header change cannot silently
+    shift a field the binding reads."""
+    import os
+    import shutil
+    import subprocess
+
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    mirrors = {"vie_grid": vie.Grid, "vie_op_info_t": vie.OpInfo, "vie_solve_opts": vie.SolveOpts,
+               "vie_solve_info": vie.SolveInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vie.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, what, val = line.split()
+        py = mirrors[cname]
+        got = ctypes.sizeof(py) if what == "size" else getattr(py, what).offset
+        assert got == int(val), (cname, what, got, val)
+
+
+def test_cp_entry_points_reject_null_operators():
+    vie = pytest.importorskip("paper_1811_00484_gb300")
+    assert vie.lib.vie_tucker_cp(None, 8, 1e-9, 100, 0, None) == 1
+    assert "NULL" in vie.lib.vie_last_error().decode()
+    assert vie.lib.vie_cp_export(None, 0, None, None, None, None, None, None) == 1
