@@ -24,8 +24,9 @@
  * DFT'd (Section V.A) and compressed by truncated HOSVD (Algorithm 1) to a
  * core of size r1 x r2 x r3 and factors U^q (P_q x r_q), eqs. (13)-(14).
  * The matvec (Section V.B) zero-pads and 3-D FFTs the current, rebuilds the
- * components from core and factors, multiplies voxel by voxel, inverse-FFTs
- * and crops.
+ * components from core and factors (or, after vie_tucker_cp, from the
+ * Tucker+CP factors of Algorithm 2, eq. (17)), multiplies voxel by voxel,
+ * inverse-FFTs and crops.
  *
  * Conventions for every call:
  *  - Arrays are C order, z fastest.  Vector fields are [B][3][n1][n2][n3]
@@ -229,10 +230,16 @@ int vie_reserve(vie_op* op, int max_batch);
 
 /*
  * Y = G J for B >= 1 vector fields (Section V.B): zero-pad, 3-D FFT, voxel-
- * wise product with the six components (rebuilt from the Tucker form, eq.
- * (13) — the last two mode products on chip at every call, from slab cores
- * core x1 U1[k1,:] formed at setup — or read from the stored spectra for
- * VIE_PATH_UNCOMPRESSED), inverse FFT, crop.  J, Y: device [B][3][n1][n2][n3] in `precision`; Y may alias J.
+ * wise product with the six components, inverse FFT, crop.  The components
+ * are rebuilt at every call from the Tucker form (VIE_PATH_TUCKER, eq. (13):
+ * the last two mode products, from slab cores core x1 U1[k1,:] formed at
+ * setup) or from the Tucker+CP factors (VIE_PATH_TUCKER_CP, eq. (17), c64
+ * only, after vie_tucker_cp), or read from the stored spectra
+ * (VIE_PATH_UNCOMPRESSED, operators built with VIE_STORE_UNCOMPRESSED).
+ * J, Y: device [B][3][n1][n2][n3] in `precision`; Y may alias J.
+ * Errors: VIE_ERR_ARG (NULL, B outside [1, 4096], a path the operator
+ * cannot serve, VIE_PATH_TUCKER_CP with VIE_C128), VIE_ERR_OOM (scratch),
+ * VIE_ERR_CUDA.
  */
 int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
                int precision, void* stream);
@@ -308,6 +315,10 @@ int vie_total_field(const vie_op* op, const void* einc, const void* w, void* E,
  * chi: device [n1][n2][n3]; rhs: device [B][3][n1][n2][n3] (e_inc or b per
  * `flags`); w: device, same layout, receives the solution (and holds x0
  * with VIE_SOLVE_X0).  Synchronises `stream` once per restart cycle.
+ * With opts->path = VIE_PATH_TUCKER_CP the inner FP32 solves apply the
+ * Tucker+CP model (eq. (17)) and the FP64 residuals the Tucker model it
+ * approximates, so the solution is that of the Tucker operator; the
+ * refinement converges only while the CP model is close enough to it.
  * Returns VIE_ERR_NO_CONVERGENCE (with `info` filled) if the limits are hit.
  */
 int vie_solve(const vie_op* op, const void* chi, const void* rhs, void* w, int B,
