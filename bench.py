@@ -40,11 +40,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
-    p.add_argument("--mode", default="solve", choices=["solve", "matvec", "solve1", "ranks", "tolerance"],
+    p.add_argument("--mode", default="solve",
+                   choices=["solve", "matvec", "solve1", "ranks", "tolerance", "refinement"],
                    help="matvec: only K timed batched matvecs; solve1: K solves only "
                         "(small commands for profilers); ranks: the multilinear rank of "
                         "the Green's tensors against frequency (Sec. VI.A, Fig. 4); tolerance: "
-                        "operator error against the HOSVD tolerance (Sec. VI.C, Fig. 7)")
+                        "operator error against the HOSVD tolerance (Sec. VI.C, Fig. 7); "
+                        "refinement: solve time and memory of the three paths as a sphere's "
+                        "grid is refined (Sec. VI.E, Fig. 9)")
     p.add_argument("--max-n", type=int, default=300, help="ranks: largest grid edge built")
     p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
     p.add_argument("--orth", type=int, default=1, choices=[1, 2],
@@ -411,6 +414,60 @@ def run_tolerance_mode(args):
         op.close()
 
 
+def run_refinement_mode(args):
+    """Scaling of the three paths as the grid of the refinement study's sphere is
+    refined (Sec. VI.E, Fig. 9): a homogeneous sphere of radius 0.15 m in a 0.3 m
+    cube, HOSVD tol 1e-8, plane wave, GMRES(50) to 1e-5 with FP64 refinement, on
+    the uncompressed, HOSVD and Tucker+CP (32 terms, 1000 ALS sweeps) paths.
+    Grid edges n = 32 .. 160 (9.4 to 1.9 mm voxels; the paper's 10 .. 2 mm with
+    the padded edge a multiple of 32).  Each path is solved twice, the second
+    solve is timed.  Memory: the six components as each path holds them (c64)."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    for n in (32, 64, 96, 128, 160):
+        if n > args.max_n:
+            continue
+        wl = workloads.sphere(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=True)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
+        einc = torch.from_numpy(wl.einc.astype(np.complex64)).cuda()
+        line = {"mode": "refinement", "n": n, "h_mm": round(1e3 * wl.h, 3),
+                "unknowns": 3 * n ** 3, "setup_s": round(setup, 3)}
+        for path in ("uncompressed", "tucker", "tucker_cp"):
+            if path == "tucker_cp":
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                errs = op.tucker_cp(32, tol=1e-12, max_iter=1000, seed=0)
+                torch.cuda.synchronize()
+                line["cp_als_s"] = round(time.perf_counter() - t0, 3)
+                line["cp_core_rel_err_max"] = max(errs)
+            try:
+                op.solve(chi, einc, tol=1e-5, path=path)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, inf = op.solve(chi, einc, tol=1e-5, path=path)
+                torch.cuda.synchronize()
+                line[path] = {"solve_ms": round(1e3 * (time.perf_counter() - t0), 2),
+                              "iterations": inf["iterations"], "refine_steps": inf["refine_steps"],
+                              "relres": inf["relres"]}
+            except vie.VieError as e:
+                line[path] = {"error": str(e)}
+        info = op.info()
+        line["max_rank"] = max(max(r) for r in info["ranks"])
+        line["bytes"] = {"uncompressed": info["uncompressed_bytes"], "tucker": info["tucker_bytes"],
+                         "tucker_cp": info["cp_bytes"]}
+        print(json.dumps(line), flush=True)
+        op.close()
+
+
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
@@ -428,6 +485,8 @@ def main():
         return run_ranks_mode(args)
     if args.mode == "tolerance":
         return run_tolerance_mode(args)
+    if args.mode == "refinement":
+        return run_refinement_mode(args)
     import numpy as np
     import torch
 

@@ -191,3 +191,20 @@ def memory_n256(count=8):
     """Memory headline at n=256 (512^3 padded), tol 1e-6, seed 3, 8 ring dipoles."""
     return make("8 ring dipoles n=256, tol 1e-6", 256, seed=3, B=1, tol_svd=1e-6,
                 incident="dipole", dipoles=ring_dipoles(count))
+
+
+def sphere(n, edge=0.3, radius=0.15, eps_r=65.0, sigma=0.6, freq_hz=FREQ_7T_HZ, tol_svd=1e-8):
+    """The refinement study's scatterer (Sec. VI.E): a homogeneous sphere of radius
+    0.15 m (eps_r = 65, sigma = 0.6 S/m) centred in a cube of edge 0.3 m resolved
+    by n voxels per axis, lit by the x-polarised plane wave.  No random draws."""
+    h = edge / n
+    x = voxel_centres(n, h)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    mask = X ** 2 + Y ** 2 + Z ** 2 <= radius ** 2
+    er = np.full((n, n, n), eps_r)
+    sg = np.full((n, n, n), sigma)
+    wl = Workload(name=f"sphere n={n}", n=(n, n, n), h=h, freq_hz=freq_hz, tol_svd=tol_svd,
+                  seed=-1, J=np.zeros((1, 3, n, n, n), dtype=np.complex128), eps_r=er,
+                  sigma=sg, mask=mask, chi=contrast_from_tissue(er, sg, mask, freq_hz))
+    wl.einc = plane_wave_x(n, n, n, h, freq_hz)
+    return wl
