@@ -85,7 +85,7 @@ __device__ __forceinline__ float2 wsum32(float2 v) {
 
 // dots: a tile is kDotThreads x kDotPacks packs; basis vectors kDotBlock at a time
 constexpr int kDotThreads = 128;
-constexpr int kDotPacks = 2;
+constexpr int kDotPacks = 4;
 constexpr int kDotBlock = 4;
 constexpr int kMaxDotCtas = 4096;             // per right-hand side (bounds the partials)
 // update: one pack per thread, basis vectors kUpdBlock at a time
