@@ -19,6 +19,7 @@ decompositions"):
               and via FFT; the J-block system operator of eq. (4).
   hosvd.py    Algorithm 1 (HOSVD), eqs. (13)-(14), Definitions A.2-A.3.
   cp.py       Algorithm 2 (Tucker+CP: CP-ALS on the HOSVD core), eq. (17).
+  factorwise.py  Section V.A: embedding and DFT applied to the Tucker factors.
   gmres.py    Section VI.C: restarted GMRES.
   adjoint.py  adjoint operator and the contrast gradient of a field misfit.
 
@@ -28,4 +29,4 @@ equivalent-sphere self term and the point-sampled off-diagonal entries are a
 stand-in for the paper's Galerkin PWL integrals, whose physics fidelity is
 parity unpinned (only the formulas themselves are pinned).
 """
-from . import kernel, embed, matvec, hosvd, cp, gmres, adjoint  # noqa: F401
+from . import kernel, embed, matvec, hosvd, cp, factorwise, gmres, adjoint  # noqa: F401
