@@ -47,7 +47,7 @@ def parse():
                         "the Green's tensors against frequency (Sec. VI.A, Fig. 4); tolerance: "
                         "operator error against the HOSVD tolerance (Sec. VI.C, Fig. 7); "
                         "refinement: solve time and memory of the three paths as a sphere's "
-                        "grid is refined (Sec. VI.E, Fig. 9)")
+                        "grid is refined (Sec. VI.D, Fig. 9)")
     p.add_argument("--max-n", type=int, default=300, help="ranks: largest grid edge built")
     p.add_argument("--no-graph", action="store_true", help="solve1: direct launches")
     p.add_argument("--orth", type=int, default=1, choices=[1, 2],
@@ -426,7 +426,7 @@ def run_tolerance_mode(args):
 
 def run_refinement_mode(args):
     """Scaling of the three paths as the grid of the refinement study's sphere is
-    refined (Sec. VI.E, Fig. 9): a homogeneous sphere of radius 0.15 m in a 0.3 m
+    refined (Sec. VI.D, Fig. 9): a homogeneous sphere of radius 0.15 m in a 0.3 m
     cube, HOSVD tol 1e-8, plane wave, GMRES(50) to 1e-5 with FP64 refinement, on
     the uncompressed, HOSVD and Tucker+CP (32 terms, 1000 ALS sweeps) paths.
     Grid edges n = 32 .. 160 (9.4 to 1.9 mm voxels; the paper's 10 .. 2 mm with

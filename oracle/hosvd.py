@@ -86,12 +86,6 @@ def tucker_full(core: np.ndarray, factors) -> np.ndarray:
     return A
 
 
-def tucker_entry(core, factors, i, j, k):
-    """eq. (13) for one entry: sum_{a,b,c} core[a,b,c] U1[i,a] U2[j,b] U3[k,c]."""
-    U1, U2, U3 = factors
-    return complex(np.einsum("abc,a,b,c->", core, U1[i], U2[j], U3[k]))
-
-
 def compress_components(Ghat: np.ndarray, tol: float, rule: str = "tail"):
     """HOSVD of each of the six FFT'd components ("each component", Section V.B)."""
     return [hosvd(Ghat[c], tol, rule) for c in range(Ghat.shape[0])]
@@ -100,11 +94,3 @@ def compress_components(Ghat: np.ndarray, tol: float, rule: str = "tail"):
 def rebuild_components(compressed) -> np.ndarray:
     """The six rebuilt spectra A~_c as one array [6, P1, P2, P3]."""
     return np.stack([tucker_full(core, U) for core, U, _ in compressed])
-
-
-def tucker_bytes(compressed, bytes_per_complex: int = 8) -> int:
-    """Storage of cores and factors (complex64 by default)."""
-    total = 0
-    for core, U, _ in compressed:
-        total += core.size + sum(u.size for u in U)
-    return total * bytes_per_complex

@@ -141,3 +141,32 @@ def test_dipole_field_is_zz_column():
     e = K.dipole_field(p[None], src, K0)[:, 0]
     G = K.dyadic(p - src, K0)
     assert np.allclose(e, [G[2], G[4], G[5]])
+
+
+@pytest.mark.parametrize("n", [(3, 4, 5), (4, 3, 2)])
+def test_dipole_incident_at_hand_placed_voxel_centres(n):
+    """dipole_incident samples dipole_field at the voxel centres (i + 1/2 - n/2) h,
+    box centre at the origin: written out here by hand for odd and even edges."""
+    h = 0.01
+    centres = {2: (-0.005, 0.005), 3: (-0.01, 0.0, 0.01), 4: (-0.015, -0.005, 0.005, 0.015),
+               5: (-0.02, -0.01, 0.0, 0.01, 0.02)}
+    src = np.array([[0.003, -0.021, 0.0071], [-0.05, 0.04, 0.1]])
+    e = K.dipole_incident(*n, h, K0, src)
+    assert e.shape == (2, 3) + n
+    for b in range(2):
+        for i, x in enumerate(centres[n[0]]):
+            for j, y in enumerate(centres[n[1]]):
+                for k, z in enumerate(centres[n[2]]):
+                    ref = K.dipole_field(np.array([x, y, z]), src[b], K0)
+                    assert np.allclose(e[b, :, i, j, k], ref, rtol=1e-13, atol=0.0)
+
+
+def test_dipole_incident_mirror_symmetry_about_the_box_centre():
+    """A z-dipole at the origin of an even grid: e_z is even and e_x odd under
+    x -> -x, which holds only if the voxel centres are symmetric about the box
+    centre (a shift of the centres by h/2 breaks it)."""
+    n = 4
+    e = K.dipole_incident(n, n, n, 0.01, K0, np.zeros((1, 3)))[0]
+    assert np.allclose(e[2], e[2][::-1], rtol=1e-13, atol=0.0)
+    assert np.allclose(e[0], -e[0][::-1], rtol=1e-13, atol=0.0)
+    assert np.allclose(e[2], e[2][:, :, ::-1], rtol=1e-13, atol=0.0)

@@ -194,7 +194,7 @@ def memory_n256(count=8):
 
 
 def sphere(n, edge=0.3, radius=0.15, eps_r=65.0, sigma=0.6, freq_hz=FREQ_7T_HZ, tol_svd=1e-8):
-    """The refinement study's scatterer (Sec. VI.E): a homogeneous sphere of radius
+    """The refinement study's scatterer (Sec. VI.D): a homogeneous sphere of radius
     0.15 m (eps_r = 65, sigma = 0.6 S/m) centred in a cube of edge 0.3 m resolved
     by n voxels per axis, lit by the x-polarised plane wave.  No random draws."""
     h = edge / n
