@@ -118,7 +118,8 @@ typedef struct vie_op_info_t {
     size_t uncompressed_bytes;   /* six c64 spectra, 6 P1 P2 P3 x 8 bytes       */
     size_t workspace_bytes;      /* scratch currently held                      */
     int has_uncompressed;        /* VIE_STORE_UNCOMPRESSED was given            */
-    int max_batch;               /* batch size the scratch is sized for         */
+    int max_batch;               /* c64 batch size the matvec scratch serves
+                                    (half of it in c128)                        */
     int line_threads[4];         /* CTA size of the x, y, inverse y, inverse x
                                     FFT stages (vie_autotune's choice)          */
     int tuned_batch;             /* batch vie_autotune timed at (0 = defaults)  */
@@ -248,11 +249,10 @@ int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path,
  * Y = G J like vie_matvec with path VIE_PATH_TUCKER and precision VIE_C64,
  * but without allocating any memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
- * they need a product, for example code being captured into a CUDA graph
- * (cudaMalloc is not allowed during capture), serving loops whose device
- * memory is owned by another allocator under a fixed budget, or callbacks
- * that must not trigger the device-wide synchronisation cudaMalloc and
- * cudaFree can cause.
+ * they need a product, for example serving loops whose device memory is
+ * owned by another allocator under a fixed budget, or callbacks that must
+ * not trigger the device-wide synchronisation cudaMalloc and cudaFree can
+ * cause.
  * Its scratch is one fixed 64 MiB array compiled into the library (every
  * GPU that loads the library holds it until the process exits).  A call
  * needs 24 B (P1 n2 n3 + P1 P2 n3) bytes of it; larger grids or batches

@@ -278,7 +278,7 @@ int vie_green_spectrum(const vie_grid* grid, int c, int flags, void* out, void* 
 int vie_reserve(vie_op* op, int max_batch) {
   CLEAR_ERROR();
   VIE_TRY(check_op(op, max_batch));
-  return ensure_workspace(op, max_batch);
+  return ensure_workspace(op, max_batch, sizeof(double2));
 }
 
 int vie_matvec(const vie_op* op, const void* J, void* Y, int B, int path, int precision,

@@ -662,9 +662,15 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   constexpr bool kFs = (R == 2 || R == 4 || R == 6);
   const bool fs = kFs && (STORED || a.octant != nullptr);
   const size_t fs_smem = fused_fs_smem(4 * R, a.H3);
+  // P3 = 512: the three-pass radix-8 kernel (tp512.cu)
+  const bool tp = (R == 16) && fused_tp_supported(a, STORED);
   if (STORED || a.octant == nullptr) {
     ProfScope ps(fam, s);
     a.g0 = 0;
+    if (tp) {
+      launch_fused_tp(a, a.H1 * a.H2, STORED, s);
+      return;
+    }
     if constexpr (kFs) {
       if (fs) {
         launch_pdl(fused_fs_kernel<4 * R, STORED>, dim3(a.H1 * a.H2), dim3(96), fs_smem, s, a);
@@ -684,6 +690,10 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
     a.g0 = k1a * a.H2;
     ProfScope ps(fam, s);
     bool done = false;
+    if (tp) {
+      launch_fused_tp(a, nk1 * a.H2, STORED, s);
+      done = true;
+    }
     if constexpr (kFs) {
       if (fs) {
         launch_pdl(fused_fs_kernel<4 * R, STORED>, dim3(nk1 * a.H2), dim3(96), fs_smem, s, a);

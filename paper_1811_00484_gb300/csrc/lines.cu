@@ -184,7 +184,7 @@ static bool launch_warp(const LineArgs<float>& a, cudaStream_t s) {
     case 8: launch_warp_r<8>(a, s); return true;
     case 10: launch_warp_r<10>(a, s); return true;
     case 12: launch_warp_r<12>(a, s); return true;
-    case 16: launch_warp_r<16>(a, s); return true;
+    case 16: if (!launch_line_tp(a, s)) launch_warp_r<16>(a, s); return true;
     default: return false;
   }
 }

@@ -17,15 +17,15 @@ template <typename T>
 int launch_fused(const vie_op* op, cx<T>* data, int B, bool stored, const int* active,
                  cudaStream_t s, bool first_chunk_ready, bool cp);
 
-size_t workspace_bytes_for(const vie_op* op, int B) {
+size_t workspace_bytes_for(const vie_op* op, int B, size_t elem) {
   const size_t n1 = op->n[0], n2 = op->n[1], n3 = op->n[2];
   const size_t P1 = op->P[0], P2 = op->P[1];
+  (void)n1;
   const size_t per = 3 * (P1 * n2 * n3 + P1 * P2 * n3);   // T1 + T2 elements per RHS
-  return per * (size_t)B * sizeof(double2);                // sized for the FP64 path
+  return per * (size_t)B * elem;
 }
 
-int ensure_workspace(vie_op* op, int B) {
-  const size_t need = workspace_bytes_for(op, B);
+int ensure_workspace_bytes(vie_op* op, size_t need) {
   if (op->ws.bytes >= need) return VIE_OK;
   if (op->ws.ptr) {
     cudaDeviceSynchronize();
@@ -41,8 +41,12 @@ int ensure_workspace(vie_op* op, int B) {
     return VIE_ERR_OOM;
   }
   op->ws.bytes = need;
-  op->ws_batch = B;
+  op->ws_batch = (int)(need / workspace_bytes_for(op, 1, sizeof(float2)));
   return VIE_OK;
+}
+
+int ensure_workspace(vie_op* op, int B, size_t elem) {
+  return ensure_workspace_bytes(op, workspace_bytes_for(op, B, elem));
 }
 
 // Arguments of the four line stages for one operator and batch, T1 then T2 in `ws`.
@@ -217,8 +221,8 @@ template <typename T>
 int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, int pro_flags,
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
                 cudaStream_t s, const double* rscale, long long rscale_stride, int mv_flags) {
-  if (workspace_bytes_for(op, B) > op->ws.bytes) {
-    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B));
+  if (workspace_bytes_for(op, B, sizeof(cx<T>)) > op->ws.bytes) {
+    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B, sizeof(cx<T>)));
   }
   return matvec_run<T>(op, op->ws.ptr, in, out, B, path, pro_flags, epi_flags, chi, addend, active,
                        s, rscale, rscale_stride, mv_flags);

@@ -119,7 +119,7 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
   long long lstart[4] = {0, 0, 0, 0}, fstart = 0;
   for (int p = 0; p < count; ++p) {
     const vie_op* op = ops[p];
-    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B[p]));
+    VIE_TRY(ensure_workspace(const_cast<vie_op*>(op), B[p], sizeof(float2)));
     lines[p] = make_line_stages<float>(op, op->ws.ptr, J[p], Y[p], B[p], 0, 0, nullptr, nullptr,
                                        nullptr);
     for (int st = 0; st < 4; ++st) {
@@ -193,7 +193,7 @@ extern "C" int vie_autotune(vie_op* op, int B, void* stream) {
     return VIE_ERR_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  VIE_TRY(ensure_workspace(op, B));
+  VIE_TRY(ensure_workspace(op, B, sizeof(float2)));
   const size_t n = (size_t)B * 3 * op->n[0] * op->n[1] * op->n[2];
   float2 *J = nullptr, *Y = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

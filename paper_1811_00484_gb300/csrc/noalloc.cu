@@ -1,16 +1,19 @@
 // vie_matvec_noalloc: the FP32 Tucker matvec for callers that cannot allocate
-// device memory.  Its scratch (the two intermediate spectra of the staged
-// FFT) is a fixed array compiled into this library instead of memory that
-// vie_matvec would allocate on first use.
+// device memory when they need a product (a serving loop whose device memory
+// belongs to another allocator under a fixed budget, or a callback that must
+// not trigger the device-wide synchronisation that cudaMalloc and cudaFree can
+// cause).  Its scratch (the two intermediate spectra of the staged FFT) is a
+// fixed array compiled into this library instead of memory that vie_matvec
+// would allocate on first use.
 #include <mutex>
 
 #include "vie_internal.cuh"
 
-namespace {
-
 // 64 MiB of scratch on every GPU that loads the library, held until exit.
-constexpr size_t kScratchBytes = 64ull << 20;
-__device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+static constexpr size_t kScratchBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -40,6 +43,7 @@ int scratch_address(void** out) {
 }  // namespace
 
 extern "C" int vie_matvec_noalloc(const vie_op* op, const void* J, void* Y, int B, void* stream) {
+  clear_error();
   if (!op || !J || !Y) {
     set_error("NULL argument");
     return VIE_ERR_ARG;

@@ -387,6 +387,7 @@ static int init_tables(vie_op* op) {
   VIE_TRY(line_fft_init_attributes());
   VIE_TRY(fused_init_attributes());
   VIE_TRY(multi_init_attributes());
+  VIE_TRY(tp_init_attributes());
   for (int q = 0; q < 3; ++q) {
     const int N = op->P[q];
     if (!make_plan(N, &op->plan[q])) {

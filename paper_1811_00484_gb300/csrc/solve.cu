@@ -1048,7 +1048,10 @@ int solve_impl(const vie_op* op_c, const void* chi, const void* rhs, void* w, in
   const int m = o->restart;
   const int path = o->path;
   const int adjoint = (flags & VIE_SOLVE_ADJOINT) ? 1 : 0;
-  VIE_TRY(ensure_workspace(op, B));
+  // matvec scratch: the FP32 inner matvecs take all B right-hand sides at once;
+  // the FP64 residual matvecs go in as many right-hand sides as fit in it
+  VIE_TRY(ensure_workspace_bytes(op, std::max(workspace_bytes_for(op, B, sizeof(float2)),
+                                              workspace_bytes_for(op, 1, sizeof(double2)))));
   SolverState* st = nullptr;
   VIE_TRY(get_state(op, B, m, &st));
   (void)path;
@@ -1086,12 +1089,20 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
   int step = 0;
   for (;; ++step) {
     if (have_x) {
-      if (!adjoint)
-        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path64, 0, EPI_SUB | EPI_CHI, st->chi64, st->x,
-                                    nullptr, s));
-      else
-        VIE_TRY(matvec_impl<double>(op, st->x, st->ax64, B, path64, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB,
-                                    st->chi64, st->x, nullptr, s));
+      // A x in FP64, in groups of right-hand sides that fit the matvec scratch
+      const int sub = (int)std::max<size_t>(
+          1, std::min<size_t>(B, op->ws.bytes / workspace_bytes_for(op, 1, sizeof(double2))));
+      for (int b0 = 0; b0 < B; b0 += sub) {
+        const int nb = std::min(sub, B - b0);
+        const double2* xb = st->x + (long long)b0 * N;
+        double2* ab = st->ax64 + (long long)b0 * N;
+        if (!adjoint)
+          VIE_TRY(matvec_impl<double>(op, xb, ab, nb, path64, 0, EPI_SUB | EPI_CHI, st->chi64, xb,
+                                      nullptr, s));
+        else
+          VIE_TRY(matvec_impl<double>(op, xb, ab, nb, path64, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB,
+                                      st->chi64, xb, nullptr, s));
+      }
       mv64 += B;
     }
     {

@@ -1,0 +1,348 @@
+// Length-512 transforms of the matvec (Section V.B) for 256-voxel grid edges
+// (P = 512): the x and y line stages and the fused z stage (zero-padded
+// forward z-FFT, voxel-wise product with the rebuilt or stored spectra,
+// cropped inverse z-FFT).
+//
+// Three radix-8 passes, 64 threads per line, 8 values per thread.  With
+// n = a + 64 b (a < 64, b < 8), a = e + 8 f and k = c + 8 g + 64 h,
+//   X[c + 8g + 64h] = sum_e w8^{eh} w64^{eg} sum_f w8^{fg} w512^{ac}
+//                     sum_b w8^{bc} x[a + 64 b],
+// so
+//   pass 1 (thread a):      DFT-8 over b, twiddle w512^{a c}, store X1[c][a]
+//   pass 2 (thread (c, e)): DFT-8 over f (a = e + 8f), twiddle w64^{e g},
+//                           store X2[c][g][e]
+//   pass 3 (thread (c, g)): DFT-8 over e, giving X[c + 8g + 64h] in register h.
+// The inverse runs the three passes backwards (inverse DFT-8s, conjugate
+// twiddles), from the register layout where the forward one ends to the
+// layout where it starts, so a forward / product / inverse sequence never
+// reorders data.  Zero padding (x[n] = 0 for n >= 256: b >= 4) and cropping
+// (outputs n < 256) prune the first and last passes.
+//
+// Exchange layouts (float2 units): X1[c][a] at c LA + a, X2[c][g][e] at
+// c 72 + 9 g + e.  Each half-warp's 64-bit accesses of every pass fall in 16
+// different bank pairs (checked for both thread layouts below).
+#include "stages.cuh"
+
+namespace vie {
+
+namespace tp {
+
+constexpr int kN = 512;
+constexpr int kM = 64;            // threads per line
+constexpr int kX2 = 576;          // 8 x 72 per line
+
+__device__ __forceinline__ float2 root(const float2* roots, int e, bool inv) {
+  const float2 w = __ldg(roots + e);
+  return inv ? conjg(w) : w;
+}
+
+// DFT-8 of x[0..3] with x[4..7] = 0: X[2k] = DFT4(x)[k], X[2k+1] = DFT4(x_n w8^n)[k]
+__device__ __forceinline__ void dft8_half_in(float2* v, bool inv) {
+  const float r = 0.70710678118654752440f;
+  float2 e0 = v[0], e1 = v[1], e2 = v[2], e3 = v[3];
+  float2 o0 = v[0], o1, o2, o3;
+  if (!inv) {
+    o1 = make_float2(r * (v[1].x + v[1].y), r * (v[1].y - v[1].x));
+    o2 = mul_mi(v[2]);
+    o3 = make_float2(r * (v[3].y - v[3].x), -r * (v[3].x + v[3].y));
+  } else {
+    o1 = make_float2(r * (v[1].x - v[1].y), r * (v[1].x + v[1].y));
+    o2 = mul_i(v[2]);
+    o3 = make_float2(-r * (v[3].x + v[3].y), r * (v[3].x - v[3].y));
+  }
+  dft4(e0, e1, e2, e3, inv);
+  dft4(o0, o1, o2, o3, inv);
+  v[0] = e0; v[2] = e1; v[4] = e2; v[6] = e3;
+  v[1] = o0; v[3] = o1; v[5] = o2; v[7] = o3;
+}
+
+// pass 1 in thread a: v[b] = x[a + 64 b]  ->  X1[c][a]
+template <bool INV, bool HALF_IN>
+__device__ __forceinline__ void pass1(float2 (&v)[8], int a, const float2* roots, float2* x1, int la) {
+  if (HALF_IN) dft8_half_in(v, INV); else dft8<float2, float>(v, INV);
+#pragma unroll
+  for (int c = 1; c < 8; ++c) v[c] = v[c] * root(roots, a * c, INV);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x1[c * la + a] = v[c];
+}
+
+// pass 2 in thread (c, e): X1[c][e + 8f]  ->  X2[c][g][e]
+template <bool INV>
+__device__ __forceinline__ void pass2(int c, int e, const float2* x1, int la, float2* x2,
+                                      const float2* roots) {
+  float2 u[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) u[f] = x1[c * la + e + 8 * f];
+  dft8<float2, float>(u, INV);
+#pragma unroll
+  for (int g = 1; g < 8; ++g) u[g] = u[g] * root(roots, 8 * e * g, INV);
+#pragma unroll
+  for (int g = 0; g < 8; ++g) x2[c * 72 + 9 * g + e] = u[g];
+}
+
+// pass 3 in thread (c, g): X2[c][g][e]  ->  w[h] = X[c + 8 g + 64 h]
+template <bool INV>
+__device__ __forceinline__ void pass3(int c, int g, const float2* x2, float2 (&w)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) w[e] = x2[c * 72 + 9 * g + e];
+  dft8<float2, float>(w, INV);
+}
+
+// inverse of pass 3 in thread (c, g): w[h] = Y[c + 8g + 64h]  ->  X2[c][g][e]
+__device__ __forceinline__ void ipass3(int c, int g, float2 (&w)[8], float2* x2, const float2* roots) {
+  dft8<float2, float>(w, true);
+#pragma unroll
+  for (int e = 1; e < 8; ++e) w[e] = w[e] * root(roots, 8 * e * g, true);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x2[c * 72 + 9 * g + e] = w[e];
+}
+
+// inverse of pass 2 in thread (c, e): X2[c][g][e]  ->  X1[c][e + 8f]
+__device__ __forceinline__ void ipass2(int c, int e, const float2* x2, float2* x1, int la,
+                                       const float2* roots) {
+  float2 u[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) u[g] = x2[c * 72 + 9 * g + e];
+  dft8<float2, float>(u, true);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const int a = e + 8 * f;
+    x1[c * la + a] = (c == 0) ? u[f] : u[f] * root(roots, a * c, true);
+  }
+}
+
+// inverse of pass 1 in thread a: X1[c][a]  ->  v[b] = 512 x[a + 64 b]
+__device__ __forceinline__ void ipass1(int a, const float2* x1, int la, float2 (&v)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = x1[c * la + a];
+  dft8<float2, float>(v, true);
+}
+
+// ---------------------------------------------------------------------------
+// x / y line stage: 8 adjacent columns per CTA, 64 threads per column.
+// Thread tid: column col = tid & 7, slot t = tid >> 3.  A warp's global
+// accesses are 4 rows x 64 contiguous bytes.  X1 column stride 514, X2 578
+// (both 2 mod 16 in float2 units).
+// ---------------------------------------------------------------------------
+constexpr int kLineCols = 8;
+constexpr int kCS1 = 514, kCS2 = 578;
+constexpr size_t kLineSmem = (size_t)kLineCols * (kCS1 + kCS2) * sizeof(float2);
+
+// INV: inverse transform (conjugate roots); HALF: forward from x[n < 256]
+// (the rest zero padding) or inverse cropped to outputs n < 256
+template <bool INV, bool HALF>
+__global__ void __launch_bounds__(512, 3) line_tp_kernel(const LineArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  const int tid = threadIdx.x, col = tid & 7, t = tid >> 3;
+  float2* x1 = sm + col * kCS1;
+  float2* x2 = sm + kLineCols * kCS1 + col * kCS2;
+  const int c0 = blockIdx.x * kLineCols, o = blockIdx.y, bb = blockIdx.z;
+  pdl_trigger();
+  pdl_wait();
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
+  if (a.prof != nullptr && blockIdx.x == 0 && o == 0 && tid == 0) atomicAdd(a.prof, a.prof_batch_bytes);
+  const bool col_ok = c0 + col < a.ncol;
+  const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                       ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                       : 1.f;
+  const float2* in = a.in + bb * a.in_bs + o * a.in_os + (long long)(c0 + col);
+  float2 v[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int p = t + kM * b;
+    float2 x = make_float2(0.f, 0.f);
+    if ((INV || !HALF || b < 4) && col_ok && p < a.lin) {
+      x = in[(long long)p * a.in_ls];
+      if (!INV) {
+        if (a.flags & PRO_RSCALE) x = rs * x;
+        if (a.flags & PRO_CONJ) x = conjg(x);
+        if (a.flags & PRO_CHI) x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
+      }
+    }
+    v[b] = x;
+  }
+  pass1<INV, !INV && HALF>(v, t, a.roots, x1, 64);
+  __syncthreads();
+  pass2<INV>(t >> 3, t & 7, x1, 64, x2, a.roots);
+  __syncthreads();
+  const int c = t >> 3, g = t & 7;
+  pass3<INV>(c, g, x2, v);
+  float2* out = a.out + bb * a.out_bs + o * a.out_os + (long long)(c0 + col);
+  if (!col_ok) return;
+#pragma unroll
+  for (int h = 0; h < 8; ++h) {
+    if (INV && HALF && h >= 4) continue;
+    const int p = c + 8 * g + kM * h;
+    if (p >= a.lout) continue;
+    float2 x = v[h];
+    if (INV) {
+      x = a.scale * x;
+      if (a.flags & EPI_CONJ) x = conjg(x);
+      if (a.flags & (EPI_SUB | EPI_ADD)) {
+        if (a.flags & EPI_CHI) x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
+        float2 w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + col) + (long long)p * a.out_ls];
+        if (a.flags & EPI_RSCALE) w = rs * w;
+        x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+      }
+    }
+    out[(long long)p * a.out_ls] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused z stage: one CTA of 256 threads per (k1, k2) mirror group, 64 threads
+// per mirror line (thread tid: line l = tid >> 6, slot t = tid & 63).  Each
+// thread carries the three Cartesian components of its line through the
+// forward passes (one after another, sharing the line's exchange buffers),
+// holds their spectra at the eight frequencies c + 8g + 64h in registers,
+// forms Y = D G D J there (G the rebuilt half fibre with mirror signs D, or
+// the stored spectra), and runs the inverse passes.  The line's 256 outputs
+// overwrite its 256 inputs.
+// ---------------------------------------------------------------------------
+constexpr int kGS = 256 + 32 + 1;     // ghalf_slot(256) + 1
+constexpr int kLA = 72;               // X1 row stride of the fused layout
+constexpr size_t kFusedSmem = (size_t)(6 * kGS + 4 * kX2 + 4 * kX2) * sizeof(float2);
+
+template <bool STORED>
+__global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* ghalf = reinterpret_cast<float2*>(smem_raw);   // [6][kGS]
+  const int tid = threadIdx.x, l = tid >> 6, t = tid & 63;
+  float2* x1 = ghalf + 6 * kGS + l * kX2;
+  float2* x2 = ghalf + 6 * kGS + 4 * kX2 + l * kX2;
+  const int grp = a.g0 + blockIdx.x;
+  const int k1 = grp / a.H2, k2 = grp % a.H2;
+  const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
+  const int ny = (k2 == 0 || 2 * k2 == a.P2) ? 1 : 2;
+  const bool valid = l < nx * ny;                          // warp-uniform
+  const int ix = valid ? l / ny : 0, iy = valid ? l % ny : 0;
+  const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
+  const long long line_off = ((long long)kx * a.P2 + ky) * a.n3;
+  const int n3 = a.n3;
+  pdl_trigger();
+  pdl_wait();
+  if (a.prof != nullptr && grp == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int b = 0; b < a.B; ++b) nb += (a.active == nullptr || a.active[b]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_rhs_bytes + a.prof_launch_bytes);
+  }
+  if (!STORED) {
+    const float2* src = a.octant + ((long long)(k1 - a.oct_k1a) * a.H2 + k2) * 6 * a.H3;
+    for (int it = tid; it < 6 * a.H3; it += 256) {
+      const int cc = it / a.H3, kk = it - cc * a.H3;
+      ghalf[cc * kGS + ghalf_slot(kk)] = src[it];
+    }
+  }
+  const float sx = (STORED || !ix) ? 1.f : -1.f, sy = (STORED || !iy) ? 1.f : -1.f;
+  const int c = t >> 3, g = t & 7;
+  __syncthreads();
+  for (int b = 0; b < a.B; ++b) {
+    if (a.active != nullptr && a.active[b] == 0) continue;   // block-uniform
+    float2 s[3][8];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const float2* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+      float2 v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int p = t + kM * m;
+        v[m] = (m < 4 && valid && p < n3) ? line[p] : make_float2(0.f, 0.f);
+      }
+      pass1<false, true>(v, t, a.roots, x1, kLA);
+      __syncthreads();
+      pass2<false>(c, t & 7, x1, kLA, x2, a.roots);
+      __syncthreads();
+      pass3<false>(c, g, x2, s[comp]);
+    }
+    // Y = D G D J at f = c + 8 g + 64 h
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int f = c + 8 * g + kM * h;
+      float2 G[6];
+      float sz = 1.f;
+      if (STORED) {
+        const long long off = ((long long)kx * a.P2 + ky) * kN + f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) G[q] = __ldg(a.spec + q * a.spec_stride + off);
+      } else {
+        const bool zm = 2 * f > kN;
+        const int fold = zm ? kN - f : f;
+        sz = zm ? -1.f : 1.f;
+        const float2* gp = ghalf + ghalf_slot(fold);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) G[q] = gp[q * kGS];
+      }
+      const float2 jx = sx * s[0][h], jy = sy * s[1][h], jz = sz * s[2][h];
+      const float2 yx = cmadd(G[0], jx, cmadd(G[1], jy, G[2] * jz));
+      const float2 yy = cmadd(G[1], jx, cmadd(G[3], jy, G[4] * jz));
+      const float2 yz = cmadd(G[2], jx, cmadd(G[4], jy, G[5] * jz));
+      s[0][h] = sx * yx;
+      s[1][h] = sy * yy;
+      s[2][h] = sz * yz;
+    }
+    __syncthreads();                 // every thread is done with X2 of the forward passes
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      float2* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
+      ipass3(c, g, s[comp], x2, a.roots);
+      __syncthreads();
+      ipass2(c, t & 7, x2, x1, kLA, a.roots);
+      __syncthreads();
+      float2 v[8];
+      ipass1(t, x1, kLA, v);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int p = t + kM * m;
+        if (valid && p < n3) line[p] = v[m];
+      }
+    }
+    __syncthreads();                 // X1 is rewritten by the next right-hand side
+  }
+}
+
+}  // namespace tp
+
+// x / y stage of a length-512 line (columns contiguous in memory)
+bool launch_line_tp(LineArgs<float> a, cudaStream_t s) {
+  if (a.plan.N != tp::kN || a.in_cs != 1 || a.out_cs != 1) return false;
+  if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
+  if (a.nother > 65535 || a.nbatch > 65535) return false;
+  const bool half = a.inverse ? (2 * a.lout == tp::kN) : (2 * a.lin == tp::kN);
+  dim3 grid((a.ncol + tp::kLineCols - 1) / tp::kLineCols, a.nother, a.nbatch);
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
+  if (a.inverse)
+    launch_pdl(half ? tp::line_tp_kernel<true, true> : tp::line_tp_kernel<true, false>, grid,
+               dim3(512), tp::kLineSmem, s, a);
+  else
+    launch_pdl(half ? tp::line_tp_kernel<false, true> : tp::line_tp_kernel<false, false>, grid,
+               dim3(512), tp::kLineSmem, s, a);
+  return true;
+}
+
+// fused z stage over the mirror groups [a.g0, a.g0 + groups) (P3 = 512, n3 <= 256)
+bool fused_tp_supported(const FusedArgs<float>& a, bool stored) {
+  return a.P3 == tp::kN && 2 * a.n3 <= tp::kN && (stored || a.octant != nullptr);
+}
+
+void launch_fused_tp(const FusedArgs<float>& a, int groups, bool stored, cudaStream_t s) {
+  if (stored)
+    launch_pdl(tp::fused_tp_kernel<true>, dim3(groups), dim3(256), tp::kFusedSmem, s, a);
+  else
+    launch_pdl(tp::fused_tp_kernel<false>, dim3(groups), dim3(256), tp::kFusedSmem, s, a);
+}
+
+}  // namespace vie
+
+int tp_init_attributes() {
+  cudaError_t e = cudaSuccess;
+  const int ls = (int)vie::tp::kLineSmem, fs = (int)vie::tp::kFusedSmem;
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
+  return e == cudaSuccess ? VIE_OK : cuda_status(e, "length-512 kernel attributes");
+}

@@ -281,7 +281,10 @@ int matvec_impl(const vie_op* op, const cx<T>* in, cx<T>* out, int B, int path, 
                 int epi_flags, const cx<T>* chi, const cx<T>* addend, const int* active,
                 cudaStream_t s, const double* rscale = nullptr, long long rscale_stride = 0,
                 int mv_flags = 0);
-int ensure_workspace(vie_op* op, int B);
+// matvec scratch T1 + T2 for B right-hand sides of `elem`-byte complex values
+// (8: FP32 path, 16: FP64 path); ensure_* grows op->ws to at least that size
+int ensure_workspace(vie_op* op, int B, size_t elem);
+int ensure_workspace_bytes(vie_op* op, size_t bytes);
 // The four line-stage launches of one matvec (x, y, inverse y, inverse x).
 template <typename T> struct LineStages {
   LineArgs<T> s[4];
@@ -297,7 +300,7 @@ int matvec_run(const vie_op* op, void* ws, const cx<T>* in, cx<T>* out, int B, i
                int pro_flags, int epi_flags, const cx<T>* chi, const cx<T>* addend,
                const int* active, cudaStream_t s, const double* rscale = nullptr,
                long long rscale_stride = 0, int mv_flags = 0);
-size_t workspace_bytes_for(const vie_op* op, int B);
+size_t workspace_bytes_for(const vie_op* op, int B, size_t elem);
 
 template <typename T> int launch_slab_cores(const vie_op* op, cudaStream_t s);
 // rebuild of the half fibres of k1 in [k1a, k1a + oct_k1) into op->oct32 (fused.cu);
@@ -332,6 +335,7 @@ int device_sms();
 int persistent_grid(const void* kernel, int threads, size_t smem, long long work);
 int fused_init_attributes();
 int multi_init_attributes();
+int tp_init_attributes();
 
 // solver (solve.cu)
 int solve_impl(const vie_op* op, const void* chi, const void* rhs, void* w, int B, int flags,

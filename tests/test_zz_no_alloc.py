@@ -1,13 +1,19 @@
-"""vie_matvec_noalloc: the Tucker matvec for callers that cannot allocate.
+"""vie_matvec_noalloc: the Tucker matvec for callers that cannot allocate
+device memory when they need a product (serving loops whose memory belongs to
+another allocator under a fixed budget, callbacks that must not trigger the
+synchronisation of cudaMalloc/cudaFree).
 
 It must give what vie_matvec gives (same tolerance as the other FP32 matvec
 tests, 1e-5 relative L2) on consecutive calls that share its fixed scratch
-array, change no device memory use after its first call, and refuse sizes
-beyond that array with VIE_ERR_ARG.  This file is collected last on purpose.
+array, agree with the FP64 oracle's FFT matvec, change no device memory use
+after its first call, and refuse sizes beyond that array with VIE_ERR_ARG.
+This file is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
+
+from oracle import embed, kernel, matvec
 import pytest
 import torch
 
@@ -47,6 +53,14 @@ def test_noalloc_matches_matvec_on_consecutive_calls(n, B):
         if call == 1:
             assert torch.cuda.mem_get_info()[0] == free_before
         assert _rel(Y, ref) <= 1e-5
+        if call == 1:
+            # against the oracle's FFT matvec on the uncompressed spectra: FP32
+            # rounding plus the HOSVD truncation (tol 1e-6, eq. (12))
+            G = embed.green_spectra(kernel.toeplitz_tensor(*n, 5e-3, kernel.wavenumber(298e6)), *n)
+            Jh = J.cpu().numpy().astype(np.complex128)
+            yo = matvec.matvec_fft(G, Jh)
+            yg = Y.cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) <= 1e-5 + 4e-6
     op.close()
 
 
