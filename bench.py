@@ -1,15 +1,19 @@
 """Benchmark of the Tucker-compressed FFT-VIE solve on GB300.
 
-Workload: the 64^3-voxel solve (128^3 padded), 5 mm voxels at 298 MHz,
-seeded ellipsoidal tissue contrast, x-polarised plane wave, HOSVD at 1e-6,
-GMRES(50) to a relative residual of 1e-6 with FP64 iterative refinement.
-One step = one complete solve (pad/FFT, Tucker rebuild + product, inverse
-FFT/crop, contrast, Arnoldi, refinement residuals).  `value` = operator
-applications (matvecs) per second over the timed solves; the same solves on
-the uncompressed-spectra path, isolated matvec rates of both paths and the
-FP64 CPU oracle are reported beside it.
+Headline workload (the memory headline): 256^3 voxels (512^3 padded), 5 mm
+voxels at 298 MHz, seeded ellipsoidal tissue contrast, 8 z-directed dipoles on
+a 0.15 m ring as right-hand sides in one batch, HOSVD at 1e-6, mixed-precision
+GMRES(50) with FP64 iterative refinement to a relative residual of 1e-5.
+One step = one GMRES(50) restart cycle of the 8-RHS system (50 Arnoldi steps:
+pad/FFT, Tucker rebuild + product, inverse FFT/crop, contrast, Gram-Schmidt,
+Givens; the cycle-end true residual) followed by its FP64 refinement residual.
+`value` = operator applications (right-hand-side matvecs, FP32 and FP64) per
+second over the timed steps.  The same steps on the uncompressed-spectra path,
+complete solves of both paths to 1e-5, the device memory of each path, the
+64^3 plane-wave solve and the FP64 CPU oracle are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--mode headline|solve64|...]
 """
 from __future__ import annotations
 
@@ -38,11 +42,15 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-n64", action="store_true", help="headline: skip the 64^3 solve summary")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
-    p.add_argument("--mode", default="solve",
-                   choices=["solve", "matvec", "solve1", "ranks", "tolerance", "refinement"],
-                   help="matvec: only K timed batched matvecs; solve1: K solves only "
+    p.add_argument("--mode", default="headline",
+                   choices=["headline", "solve64", "matvec", "solve1", "ranks", "tolerance",
+                            "refinement"],
+                   help="headline: the 256^3 8-dipole workload (default); solve64: the 64^3 "
+                        "plane-wave solve with its extras; matvec: only K timed batched matvecs; "
+                        "solve1: K solves only "
                         "(small commands for profilers); ranks: the multilinear rank of "
                         "the Green's tensors against frequency (Sec. VI.A, Fig. 4); tolerance: "
                         "operator error against the HOSVD tolerance (Sec. VI.C, Fig. 7); "
@@ -284,6 +292,318 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+HEADLINE_WORKLOAD = ("memory headline: 256^3 voxels (512^3 padded, 5 mm, 298 MHz), 8 z-dipoles on a "
+                     "0.15 m ring in one batch, HOSVD 1e-6, GMRES(50) + FP64 refinement to 1e-5; one "
+                     "step = one restart cycle of the 8-RHS system and its FP64 refinement residual")
+
+
+def headline_config(world):
+    return {"workload": HEADLINE_WORKLOAD, "global_batch": 8 * world,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs > L2 (an 8-RHS vector is 3.2 GB, the Krylov basis 164 GB): no flush needed"}
+
+
+def oracle_sample_rate(wl, J, seconds, max_voxels=None, seed=0):
+    """The oracle's plain BTTB product (oracle.matvec.matvec_at) at successive
+    uniformly drawn output voxels, for every right-hand side of J, until `seconds`
+    have passed.  Returns (right-hand-side matvecs per second, voxels, seconds,
+    threads used = process CPU time / wall time)."""
+    import numpy as np
+    from oracle import kernel, matvec
+
+    k0 = kernel.wavenumber(wl.freq_hz)
+    rng = np.random.default_rng(seed)
+    t0, c0 = time.perf_counter(), time.process_time()
+    nvox = 0
+    while True:
+        m = tuple(int(rng.integers(0, v)) for v in wl.n)
+        matvec.matvec_at(J, wl.h, k0, [m])
+        nvox += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_voxels and nvox >= max_voxels):
+            break
+    used = (time.process_time() - c0) / el
+    rate = nvox * J.shape[0] / float(np.prod(wl.n)) / el
+    return rate, nvox, el, used
+
+
+def run_reference_headline(args):
+    """Reference arm on the headline workload: the FP64 oracle's plain BTTB definition
+    at sampled output voxels (each step one voxel, all three components, the seeded
+    current J of the workload), as right-hand-side matvecs per second."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+
+    wl = workloads.memory_n256()
+    J = wl.J
+    for w in range(args.warmup):
+        oracle_sample_rate(wl, J, 0.0, max_voxels=1, seed=1000 + w)
+    t_total, v_total, used = 0.0, 0, []
+    for k in range(args.steps):
+        _, nv, el, u = oracle_sample_rate(wl, J, 0.0, max_voxels=1, seed=k)
+        t_total += el
+        v_total += nv
+        used.append(u)
+    value = v_total * J.shape[0] / float(wl.n[0] * wl.n[1] * wl.n[2]) / t_total
+    cores = max(1, round(statistics.median(used)))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": headline_config(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"the oracle's BTTB definition (kernel formed per output voxel) "
+                                       f"at {v_total} sampled output voxels of the 256^3 workload's "
+                                       f"current (3 components, 1 right-hand side) in {t_total:.1f} s; "
+                                       "one step one voxel; value = fraction of a matvec per second"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_headline(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def used_bytes():
+        free, total = torch.cuda.mem_get_info()
+        return total - free
+
+    wl = workloads.memory_n256()
+    n = wl.n
+    mem0 = used_bytes()
+    barrier()
+    t0 = time.perf_counter()
+    op = vie.Operator(n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=True)
+    barrier()
+    setup_s = time.perf_counter() - t0
+    chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
+    einc = op.incident_dipole(wl.dipoles)                    # c64 [8, 3, n, n, n]
+    B = einc.shape[0]
+    w = torch.empty_like(einc)
+    step_kw = dict(tol=1e-5, restart=50, max_outer=1, max_refine=1, refine=False,
+                   raise_on_failure=False)
+
+    def timed_steps(path, k, chi_, einc_):
+        mv = 0
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        start.record()
+        for _ in range(k):
+            _, inf = op.solve(chi_, einc_, path=path, out=w, **step_kw)
+            mv += inf["matvecs"]
+        stop.record()
+        barrier()
+        return start.elapsed_time(stop) / 1e3, mv
+
+    for _ in range(args.warmup):
+        op.solve(chi, einc, out=w, **step_kw)
+    op.solve(chi, einc, path="uncompressed", out=w, **step_kw)
+    # one step with every kernel family instrumented: the breakdown
+    vie.profile_start()
+    timed_steps("tucker", 1, chi, einc)
+    kern = vie.profile_stop()
+    dom = max((k for k in kern if kern[k]["bytes"] > 0), key=lambda k: kern[k]["ms"])
+    # timed region (the headline): no instrumentation inside the library
+    with ClockSampler(local) as clk:
+        t_tucker, mv_tucker = timed_steps("tucker", args.steps, chi, einc)
+    clocks = clk.summary()
+    k_unc = min(args.steps, 5)
+    t_unc, mv_unc = timed_steps("uncompressed", k_unc, chi, einc)
+    # the roofline kernel's launches timed with CUDA events on their stream
+    k_roof = min(args.steps, 3)
+    vie.profile_start([dom])
+    t_roof, _ = timed_steps("tucker", k_roof, chi, einc)
+    kern_live = vie.profile_stop()
+
+    # end to end: contrast and incident fields from pinned host memory, solution back
+    chi_h = torch.from_numpy(wl.chi.astype(np.complex64)).pin_memory()
+    einc_h = einc.cpu().pin_memory()
+    w_h = torch.empty_like(einc_h).pin_memory()
+    k_e2e = min(args.steps, 3)
+    barrier()
+    e2e_start = time.perf_counter()
+    mv_e2e = 0
+    for _ in range(k_e2e):
+        c_d = chi_h.to("cuda", non_blocking=True)
+        e_d = einc_h.to("cuda", non_blocking=True)
+        _, inf = op.solve(c_d, e_d, out=w, **step_kw)
+        mv_e2e += inf["matvecs"]
+        w_h.copy_(w, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    t_e2e = time.perf_counter() - e2e_start
+    del c_d, e_d
+
+    # complete refined solves of both paths to 1e-5
+    solves = {}
+    for path in ("tucker", "uncompressed"):
+        barrier()
+        ts = time.perf_counter()
+        _, inf = op.solve(chi, einc, tol=1e-5, restart=50, max_outer=200, max_refine=20, path=path,
+                          out=w)
+        barrier()
+        solves[path] = {"s": time.perf_counter() - ts, "iterations": inf["iterations"],
+                        "matvecs": inf["matvecs"], "refine_steps": inf["refine_steps"],
+                        "relres": inf["relres"], "converged": inf["converged"]}
+    peak_used = used_bytes() - mem0
+    info = op.info()
+
+    # isolated batched matvecs (the 8 incident fields), both paths
+    def matvec_ms(path, reps=3):
+        op.matvec(einc, path=path, out=w)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            op.matvec(einc, path=path, out=w)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    mv_ms = {p: matvec_ms(p) for p in ("tucker", "uncompressed")}
+    vie.profile_start()
+    op.matvec(einc, out=w)
+    kern_mv = vie.profile_stop()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, nv, el, used = oracle_sample_rate(wl, wl.J, 15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": max(1, round(used)), "kind": "oracle",
+               "sample": f"the oracle's BTTB definition at {nv} sampled output voxels of the 256^3 "
+                         f"workload's current (3 components, 1 right-hand side) in {el:.1f} s "
+                         f"(fraction of a matvec per second)"}
+
+    t_tucker, mv_all = reduce_ranks(t_tucker, mv_tucker, world)
+    t_unc, mv_unc_all = reduce_ranks(t_unc, mv_unc, world)
+    t_e2e, mv_e2e_all = reduce_ranks(t_e2e, mv_e2e, world)
+    value = mv_all / t_tucker
+    peak, peak_kind = measured_peaks()
+
+    def gbs(e):
+        return e["bytes"] / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else 0.0
+
+    tot = max(1e-9, sum(x["ms"] for x in kern.values()))
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / tot, 4),
+                   "GBps": round(gbs(v), 1)} for k, v in kern.items()}
+    d = kern_live[dom]
+    traffic = recorded_traffic(dom)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(gbs(d), 1), "peak": peak,
+                "unit": "GB/s", "frac": round(gbs(d) / peak, 4),
+                "traffic": round(traffic) if traffic is not None else None,
+                "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+                "timing": f"CUDA events around every launch of the family on its stream, over {k_roof} "
+                          "further steps",
+                "instrumented_ms_per_step": 1e3 * t_roof / k_roof,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    mb = lambda v: round(v / 1e6, 1)
+    dev_t, dev_s = info["device_bytes_tucker"], info["device_bytes_spectra"]
+    ws, sws = info["matvec_workspace_bytes"], info["solver_workspace_bytes"]
+    memory = {"unit": "MB", "ranks": info["ranks"],
+              "tucker_cores_factors_c64": mb(info["tucker_bytes"]),
+              "slab_cores_c64": mb(info["slab_bytes"]),
+              "rebuild_scratch": mb(info["rebuild_scratch_bytes"]),
+              "operator_tucker_all": mb(dev_t),
+              "operator_spectra_c64_c128": mb(dev_s),
+              "uncompressed_spectra_c64": mb(info["uncompressed_bytes"]),
+              "matvec_workspace": mb(ws), "solver_workspace": mb(sws),
+              "path_total_tucker": mb(dev_t + ws + sws),
+              "path_total_uncompressed": mb(dev_s + ws + sws),
+              "process_peak_used": mb(peak_used),
+              "setup_s": round(setup_s, 2)}
+    f = kern_mv.get("fused_tucker")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_tucker / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": headline_config(world),
+        "step": {"tucker_ms": 1e3 * t_tucker / args.steps, "uncompressed_ms": 1e3 * t_unc / k_unc,
+                 "uncompressed_matvecs_per_s": mv_unc_all / t_unc, "uncompressed_steps": k_unc,
+                 "matvecs_per_step": mv_tucker / args.steps},
+        "solve": solves,
+        "matvec": {"tucker_ms": mv_ms["tucker"], "uncompressed_ms": mv_ms["uncompressed"],
+                   "batch": B, "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                               "GBps": round(gbs(v), 1)} for k, v in kern_mv.items()}},
+        "memory": memory,
+        "clocks": clocks,
+        "e2e": {"value": mv_e2e_all / t_e2e, "unit": UNIT, "steps": k_e2e,
+                "h2d_bytes_per_step": chi_h.numel() * 8 + einc_h.numel() * 8,
+                "d2h_bytes_per_step": w_h.numel() * 8},
+        "cpu_baseline": cpu,
+        "roofline": roofline,
+        "roofline_fused_matvec": None if not f else {
+            "kernel": "fused_tucker (one batched matvec, B=8)", "bound": "hbm",
+            "achieved": round(gbs(f), 1), "peak": peak, "unit": "GB/s", "frac": round(gbs(f) / peak, 4),
+            "avg_launch_us": 1e3 * f["ms"] / f["launches"]},
+        "kernels": kernels,
+        "kernels_note": "per-family breakdown from one separately profiled step (all families "
+                        "instrumented); the timed steps run without instrumentation",
+        "gpu_launches": int(sum(v["launches"] for v in kern.values())) * args.steps,
+    }
+    if rank == 0 and not args.no_n64:
+        line["n64"] = solve64_summary(args)
+    if rank == 0:
+        print(json.dumps(line))
+    op.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def solve64_summary(args):
+    """The 64^3 plane-wave solve (GMRES(50) to 1e-6 + FP64 refinement) on both paths,
+    three solves each, and one matvec's error against the oracle."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+    from oracle import embed, kernel, matvec
+
+    wl = workloads.solve_n64()
+    op = vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd, store_uncompressed=True)
+    chi = torch.from_numpy(wl.chi.astype(np.complex64)).cuda()
+    einc = torch.from_numpy(wl.einc.astype(np.complex64)).cuda()
+    out = {"workload": "solve 64^3 voxels (128^3 padded), plane wave, HOSVD 1e-6, GMRES(50) to 1e-6 "
+                       "+ FP64 refinement"}
+    for path in ("tucker", "uncompressed"):
+        op.solve(chi, einc, tol=1e-6, path=path)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mv = 0
+        for _ in range(3):
+            _, inf = op.solve(chi, einc, tol=1e-6, path=path)
+            mv += inf["matvecs"]
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        out[path] = {"ms_per_solve": ms, "matvecs_per_s": mv / (3 * ms * 1e-3),
+                     "iterations": inf["iterations"], "relres": inf["relres"]}
+    k0 = kernel.wavenumber(wl.freq_hz)
+    Ghat = embed.green_spectra(kernel.toeplitz_tensor(*wl.n, wl.h, k0), *wl.n)
+    ref = matvec.matvec_fft(Ghat, wl.J)
+    y = op.matvec(torch.from_numpy(wl.J.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    out["matvec_rel_err_vs_oracle"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    inf = op.info()
+    out["memory_MB"] = {"operator_tucker_all": round(inf["device_bytes_tucker"] / 1e6, 2),
+                        "uncompressed_spectra_c64": round(inf["uncompressed_bytes"] / 1e6, 2)}
+    op.close()
+    return out
+
+
 def run_solve1_mode(args):
     """K solves of the bench workload and nothing else (for ncu captures)."""
     import numpy as np
@@ -486,7 +806,7 @@ def main():
     if args.record_traffic:
         return record_traffic(args)
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference(args) if args.mode == "solve64" else run_reference_headline(args)
     if args.mode == "matvec":
         return run_matvec_mode(args)
     if args.mode == "solve1":
@@ -497,6 +817,14 @@ def main():
         return run_tolerance_mode(args)
     if args.mode == "refinement":
         return run_refinement_mode(args)
+    if args.mode == "solve64":
+        return run_solve64(args)
+    return run_headline(args)
+
+
+def run_solve64(args):
+    """The 64^3 plane-wave solve (GMRES(50) to 1e-6, FP64 refinement): one step is one
+    complete solve; with isolated matvecs, cuFFT, Tucker+CP and the 96^3 batch."""
     import numpy as np
     import torch
 

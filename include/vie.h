@@ -134,6 +134,16 @@ typedef struct vie_op_info_t {
                                     the Tucker model                           */
     int cp_sweeps[6];            /* ALS sweeps taken per component             */
     size_t cp_bytes;             /* c64 Tucker+CP factors W^q (half rows)      */
+    size_t device_bytes_tucker;  /* all device memory the operator holds for the
+                                    compressed paths: c64 and c128 cores and
+                                    half factors, slab cores, the rebuild's U3
+                                    fragments and scratch, Tucker+CP factors,
+                                    metadata and FFT root tables               */
+    size_t device_bytes_spectra; /* stored spectra, c64 and c128 (0 without
+                                    VIE_STORE_UNCOMPRESSED)                     */
+    size_t matvec_workspace_bytes; /* matvec scratch T1 + T2 currently held     */
+    size_t solver_workspace_bytes; /* Krylov basis, Hessenberg, refinement
+                                    vectors currently held (vie_solve)         */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */

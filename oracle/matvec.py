@@ -9,7 +9,10 @@ components).  It is computed two ways:
   * ``matvec_fft``         - zero-pad to (2 n1, 2 n2, 2 n3), 3-D DFT, multiply
                              voxel by voxel with the FFT'd circulant components,
                              inverse DFT, crop (Section V.B, the "traditional"
-                             FFT-based product).
+                             FFT-based product);
+  * ``matvec_at``          - the definition evaluated only at chosen output
+                             voxels, with the kernel formed on the fly, for
+                             grids too large for the other two.
 The system operator of the J-block of eq. (4), rescaled to w = j / c_e, is
   A w = w - chi * (G w),   right-hand side  chi * e_inc.
 """
@@ -17,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .kernel import component_index
+from .kernel import COMPONENTS, component_index, dyadic, self_term
 
 
 def _as_batch(J):
@@ -96,3 +99,29 @@ def dense_operator(T: np.ndarray, n1: int, n2: int, n3: int) -> np.ndarray:
         for b in range(3):
             G[a * N:(a + 1) * N, b * N:(b + 1) * N] = T[component_index(a, b)][idx]
     return G
+
+
+def matvec_at(J: np.ndarray, h: float, k0: float, voxels, self_mode: str = "full") -> np.ndarray:
+    """(G J)_a[m] = sum_b sum_{m'} T_ab[m - m'] J_b[m'] at the output voxels m in
+    ``voxels`` (index triples), for every right-hand side of J [B, 3, n1, n2, n3]
+    (or [3, n1, n2, n3]).  T_ab[r] is h^3 times the dyadic kernel at offset r h,
+    and the self term at r = 0 (the entries of kernel.toeplitz_tensor), formed
+    here only for the offsets one output voxel needs.  Returns [B, S, 3]
+    (or [S, 3])."""
+    Jb, single = _as_batch(J)
+    n1, n2, n3 = Jb.shape[-3:]
+    i, j, k = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    out = np.zeros((Jb.shape[0], len(voxels), 3), dtype=np.complex128)
+    for s_, m in enumerate(voxels):
+        m = tuple(int(v) for v in m)
+        R = np.stack([(m[0] - i) * h, (m[1] - j) * h, (m[2] - k) * h], axis=-1)
+        R[m] = (1.0, 0.0, 0.0)                 # placeholder for the zero offset
+        T = dyadic(R, k0) * h ** 3
+        st = self_term(h, k0, self_mode)
+        for c, (a, b) in enumerate(COMPONENTS):
+            T[(c,) + m] = st if a == b else 0.0
+        for a in range(3):
+            for b in range(3):
+                Tab = T[component_index(a, b)].ravel()
+                out[:, s_, a] += Jb[:, b].reshape(Jb.shape[0], -1) @ Tab
+    return out[0] if single else out

@@ -61,7 +61,9 @@ class OpInfo(ctypes.Structure):
                 ("line_threads", ctypes.c_int * 4), ("tuned_batch", ctypes.c_int),
                 ("rebuild_kernel", ctypes.c_int), ("cp_rank", ctypes.c_int),
                 ("cp_rel_err", ctypes.c_double * 6), ("cp_sweeps", ctypes.c_int * 6),
-                ("cp_bytes", ctypes.c_size_t)]
+                ("cp_bytes", ctypes.c_size_t), ("device_bytes_tucker", ctypes.c_size_t),
+                ("device_bytes_spectra", ctypes.c_size_t), ("matvec_workspace_bytes", ctypes.c_size_t),
+                ("solver_workspace_bytes", ctypes.c_size_t)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -221,7 +223,11 @@ class Operator:
                 "line_threads": tuple(inf.line_threads), "tuned_batch": inf.tuned_batch,
                 "rebuild_kernel": REBUILD_KERNELS[inf.rebuild_kernel],
                 "cp_rank": inf.cp_rank, "cp_rel_err": tuple(inf.cp_rel_err),
-                "cp_sweeps": tuple(inf.cp_sweeps), "cp_bytes": inf.cp_bytes}
+                "cp_sweeps": tuple(inf.cp_sweeps), "cp_bytes": inf.cp_bytes,
+                "device_bytes_tucker": inf.device_bytes_tucker,
+                "device_bytes_spectra": inf.device_bytes_spectra,
+                "matvec_workspace_bytes": inf.matvec_workspace_bytes,
+                "solver_workspace_bytes": inf.solver_workspace_bytes}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""
@@ -354,7 +360,9 @@ PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy
 
 def _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph, refine, orth):
     if inner_tol is None:
-        inner_tol = max(tol, 1e-5) if refine else tol
+        # the first inner solve aims below the target, so that FP32 rounding of its
+        # residual estimate does not cost a second refinement step
+        inner_tol = max(0.5 * tol, 1e-7) if refine else tol
     return SolveOpts(float(tol), int(restart), int(max_outer), float(inner_tol), int(max_refine),
                      PATHS[path], int(bool(use_graph)), int(bool(refine)), int(orth))
 

@@ -205,6 +205,32 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
     r.cp_sweeps[c] = op->cp.sweeps[c];
   }
   r.cp_bytes = op->cp.R == 0 ? 0 : (size_t)6 * (op->H[0] + op->H[1] + op->H[2]) * op->cp.R * sizeof(float2);
+  // device memory held for the Tucker path: cores and half factors in both
+  // precisions, the transposed FP32 U3, slab cores in both precisions, the U3
+  // fragments and rebuild scratch of the FP32 rebuild, metadata, root tables
+  size_t tb = 0;
+  for (int c = 0; c < 6; ++c) {
+    const TuckerComp& tc = op->comp[c];
+    tb += (size_t)tc.r[0] * tc.r[1] * tc.r[2] * (sizeof(float2) + sizeof(double2));
+    for (int q = 0; q < 3; ++q) tb += (size_t)op->H[q] * tc.r[q] * (sizeof(float2) + sizeof(double2));
+    if (tc.U3t32) tb += (size_t)op->H[2] * tc.r[2] * sizeof(float2);
+  }
+  tb += 6 * op->slab_stride * (sizeof(float2) + sizeof(double2));
+  if (op->u3frag) tb += 6ull * op->tc_nsplit * op->tc_ks * op->tc_ntc * 32 * sizeof(uint4);
+  tb += r.rebuild_scratch_bytes;
+  tb += 12 * sizeof(CompMeta<float>);
+  for (int q = 0; q < 3; ++q) tb += (size_t)op->P[q] * (sizeof(float2) + sizeof(double2));
+  if (op->cp.R > 0) {
+    tb += r.cp_bytes * 3;                                          // W32 and W64
+    tb += 6ull * op->H[2] * op->cp.R * sizeof(float2);             // W3 transposed
+    tb += 6ull * op->cp.nsplit * op->cp.ks * op->cp.ntc * 32 * sizeof(uint4);
+  }
+  r.device_bytes_tucker = tb;
+  r.device_bytes_spectra = op->spec32 ? 6ull * op->P[0] * op->P[1] * op->P[2] *
+                                            (sizeof(float2) + sizeof(double2))
+                                      : 0;
+  r.matvec_workspace_bytes = op->ws.bytes;
+  r.solver_workspace_bytes = op->solve_ws.bytes;
   *info = r;
   return VIE_OK;
 }

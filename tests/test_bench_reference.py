@@ -20,4 +20,7 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
-    assert line["config"]["workload"].startswith("solve 64^3 voxels")
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.headline_config(1)
+    assert line["config"]["workload"].startswith("memory headline: 256^3 voxels")
