@@ -485,6 +485,7 @@ void vie_destroy(vie_op* op) {
     cudaFree(op->roots64[q]);
   }
   cudaFree(op->meta);
+  cudaFree(op->dev_err);
   cudaFree(op->ws.ptr);
   cudaFree(op->solve_ws.ptr);
   delete op;

@@ -157,6 +157,7 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
     st.s[i].threads = op->tune.line_threads[i];
     st.s[i].rscale = rscale;
     st.s[i].rscale_stride = rscale_stride;
+    st.s[i].err = op->dev_err;
   }
   return st;
 }

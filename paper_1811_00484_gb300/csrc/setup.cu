@@ -602,6 +602,8 @@ static int finish_operator(vie_op* op) {
                               tc.r[1], tc.r[2], tc.s[0], tc.s[1], tc.s[2]};
   }
   static_assert(sizeof(CompMeta<float>) == sizeof(CompMeta<double>), "meta layout");
+  VIE_TRY(dalloc(&op->dev_err, sizeof(int)));
+  VIE_CUDA(cudaMemset(op->dev_err, 0, sizeof(int)));
   VIE_TRY(dalloc((char**)&op->meta, sizeof(m32) + sizeof(m64)));
   VIE_CUDA(cudaMemcpy(op->meta, m32, sizeof(m32), cudaMemcpyHostToDevice));
   VIE_CUDA(cudaMemcpy(static_cast<char*>(op->meta) + sizeof(m32), m64, sizeof(m64),

@@ -21,7 +21,10 @@
 // Exchange layouts (float2 units): X1[c][a] at c LA + a, X2[c][g][e] at
 // c 72 + 9 g + e.  Each half-warp's 64-bit accesses of every pass fall in 16
 // different bank pairs (checked for both thread layouts below).
+#include <algorithm>
+
 #include "stages.cuh"
+#include "tma.cuh"
 
 namespace vie {
 
@@ -118,6 +121,69 @@ __device__ __forceinline__ void ipass1(int a, const float2* x1, int la, float2 (
   dft8<float2, float>(v, true);
 }
 
+// Per-slot twiddle table in shared memory, [22][64] (row j, slot t):
+//   rows 0..6   w512^{t c},             c = 1..7        (pass 1)
+//   rows 7..13  w64^{(t mod 8) x},      x = 1..7        (pass 2, inverse pass 3)
+//   rows 14..21 w512^{(t mod 8 + 8 f) (t div 8)}, f = 0..7   (inverse pass 2)
+// The same for every line, tile and right-hand side a thread handles.
+constexpr int kTwRows = 22;
+__device__ __forceinline__ void fill_twiddles(float2* tw, const float2* roots, int tid, int nth) {
+  for (int i = tid; i < kTwRows * kM; i += nth) {
+    const int j = i / kM, t = i % kM;
+    int e;
+    if (j < 7) e = t * (j + 1);
+    else if (j < 14) e = 8 * (t & 7) * (j - 6);
+    else e = ((t & 7) + 8 * (j - 14)) * (t >> 3);
+    tw[i] = roots[e];
+  }
+}
+__device__ __forceinline__ float2 twv(const float2* tw, int row, int t, bool inv) {
+  const float2 w = tw[row * kM + t];
+  return inv ? conjg(w) : w;
+}
+
+template <bool INV, bool HALF_IN>
+__device__ __forceinline__ void pass1t(float2 (&v)[8], int a, const float2* tw, float2* x1, int la) {
+  if (HALF_IN) dft8_half_in(v, INV); else dft8<float2, float>(v, INV);
+#pragma unroll
+  for (int c = 1; c < 8; ++c) v[c] = v[c] * twv(tw, c - 1, a, INV);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x1[c * la + a] = v[c];
+}
+
+// pass 2 up to its twiddles (the caller stores u[g] at X2[c][g][e]); slot t = 8 c + e
+template <bool INV>
+__device__ __forceinline__ void pass2t_load(float2 (&u)[8], int t, const float2* x1, int la,
+                                            const float2* tw) {
+  const int c = t >> 3, e = t & 7;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) u[f] = x1[c * la + e + 8 * f];
+  dft8<float2, float>(u, INV);
+#pragma unroll
+  for (int g = 1; g < 8; ++g) u[g] = u[g] * twv(tw, 6 + g, t, INV);
+}
+
+// inverse of pass 3 in slot t = 8 c + g
+__device__ __forceinline__ void ipass3t(int t, float2 (&w)[8], float2* x2, const float2* tw) {
+  const int c = t >> 3, g = t & 7;
+  dft8<float2, float>(w, true);
+#pragma unroll
+  for (int e = 1; e < 8; ++e) w[e] = w[e] * twv(tw, 6 + e, t, true);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x2[c * 72 + 9 * g + e] = w[e];
+}
+
+// inverse of pass 2 in slot t = 8 c + e
+__device__ __forceinline__ void ipass2t(int t, const float2* x2, float2* x1, int la, const float2* tw) {
+  const int c = t >> 3, e = t & 7;
+  float2 u[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) u[g] = x2[c * 72 + 9 * g + e];
+  dft8<float2, float>(u, true);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) x1[c * la + e + 8 * f] = u[f] * twv(tw, 14 + f, t, true);
+}
+
 // ---------------------------------------------------------------------------
 // x / y line stage: 8 adjacent columns per CTA, 64 threads per column.
 // Thread tid: column col = tid & 7, slot t = tid >> 3.  A warp's global
@@ -191,6 +257,171 @@ __global__ void __launch_bounds__(512, 3) line_tp_kernel(const LineArgs<float> a
 }
 
 // ---------------------------------------------------------------------------
+// The same line stage as a persistent kernel whose input tiles arrive by TMA:
+// each CTA walks its tiles (8 columns x one line position range) through a
+// ring of `nstage` input buffers, so that the next tiles' copies are in
+// flight while the current one is transformed; one exchange buffer serves
+// as X1 and then as X2.  A tile is one or two boxes of 256 rows x 8 columns,
+// stored [row][column].
+// ---------------------------------------------------------------------------
+constexpr size_t kPipeX = (size_t)kLineCols * kCS2 * sizeof(float2);   // X1 / X2 (37 KB)
+constexpr size_t kTwBytes = (size_t)kTwRows * kM * sizeof(float2);       // 11 KB
+constexpr unsigned kWaitPolls = 1u << 22;
+constexpr int kMaxStages = 4;
+
+struct PipeTiles {
+  int ncg;              // column groups
+  int ntiles;           // ncg * nother * nbatch
+  int rows;             // input rows per tile (256 or 512)
+  int p_dim;            // tensor-map dimension of the line position (1 or 2; the other is `o`)
+  int nstage;           // ring depth (2 .. kMaxStages)
+};
+
+__host__ __device__ constexpr size_t pipe_stage_bytes(int rows) {
+  return (size_t)rows * kLineCols * sizeof(float2);
+}
+__host__ __device__ constexpr size_t pipe_smem(int rows, int nstage) {
+  return (size_t)nstage * pipe_stage_bytes(rows) + kPipeX + kTwBytes + kMaxStages * sizeof(uint64_t) +
+         1024;
+}
+
+template <bool INV, bool HALF>
+__global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> a,
+                                                        const __grid_constant__ CUtensorMap map,
+                                                        const PipeTiles pt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int sbytes = (int)pipe_stage_bytes(pt.rows);
+  const int NS = pt.nstage;
+  auto stage = [&](int s) { return reinterpret_cast<float2*>(base + s * sbytes); };
+  float2* xb = reinterpret_cast<float2*>(base + NS * sbytes);
+  float2* tw = reinterpret_cast<float2*>(base + NS * sbytes + kPipeX);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + NS * sbytes + kPipeX + kTwBytes);
+  const int tid = threadIdx.x, col = tid & 7, t = tid >> 3;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  fill_twiddles(tw, a.roots, tid, blockDim.x);
+  __syncthreads();
+  pdl_trigger();
+  pdl_wait();
+  const int per_bb = pt.ncg * a.nother;
+  const int G = gridDim.x;
+  auto next_tile = [&](int from) {
+    if (a.active == nullptr) return from < pt.ntiles ? from : pt.ntiles;
+    for (int q = from; q < pt.ntiles; q += G)
+      if (a.active[(q / per_bb) / a.batch_per_rhs] != 0) return q;
+    return pt.ntiles;
+  };
+  const int box_rows = pt.rows < 256 ? pt.rows : 256;
+  auto issue = [&](int tile, int s) {
+    const int cg = tile % pt.ncg, rest = tile / pt.ncg;
+    const int o = rest % a.nother, bb = rest / a.nother;
+    mbar_arrive_expect_tx(&bar[s], (unsigned)sbytes);
+    for (int p0 = 0; p0 < pt.rows; p0 += box_rows) {
+      const int c1 = pt.p_dim == 1 ? p0 : o, c2 = pt.p_dim == 1 ? o : p0;
+      tma_load_4d(stage(s) + p0 * kLineCols, &map, cg * kLineCols, c1, c2, bb, &bar[s]);
+    }
+  };
+  // the ring holds the tile cur and the next NS - 1 ones (last_issued is the newest)
+  int cur = next_tile(blockIdx.x);
+  int last_issued = cur;
+  if (tid == 0 && cur < pt.ntiles) issue(cur, 0);
+  for (int q = 1; q < NS; ++q) {
+    last_issued = last_issued < pt.ntiles ? next_tile(last_issued + G) : pt.ntiles;
+    if (tid == 0 && last_issued < pt.ntiles) issue(last_issued, q);
+  }
+  if (a.prof != nullptr && blockIdx.x == 0 && tid == 0) {
+    unsigned long long nb = 0;
+    for (int bb = 0; bb < a.nbatch; ++bb)
+      nb += (a.active == nullptr || a.active[bb / a.batch_per_rhs]) ? 1 : 0;
+    atomicAdd(a.prof, nb * a.prof_batch_bytes);
+  }
+  const int c = t >> 3, g = t & 7;
+  int s = 0;
+  unsigned phase_bits = 0;                        // bit q: parity of the next wait on stage q
+  while (cur < pt.ntiles) {
+    const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, kWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.err != nullptr) atomicExch(a.err, VIE_ERR_TIMEOUT);
+      for (int q = 0; q < NS; ++q) mbar_wait_bounded(&bar[q], (phase_bits >> q) & 1u, kWaitPolls);
+      return;
+    }
+    phase_bits ^= 1u << s;
+    const int cg = cur % pt.ncg, rest = cur / pt.ncg;
+    const int o = rest % a.nother, bb = rest / a.nother;
+    const int c0 = cg * kLineCols;
+    const bool col_ok = c0 + col < a.ncol;
+    const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                         ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                         : 1.f;
+    const float2* S = stage(s) + col;
+    float2 v[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int p = t + kM * b;
+      float2 x = make_float2(0.f, 0.f);
+      if ((INV || !HALF || b < 4) && p < pt.rows) {
+        x = S[p * kLineCols];
+        if (!INV) {
+          if (a.flags & PRO_RSCALE) x = rs * x;
+          if (a.flags & PRO_CONJ) x = conjg(x);
+          if ((a.flags & PRO_CHI) && col_ok)
+            x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
+        }
+      }
+      v[b] = x;
+    }
+    __syncthreads();                       // stage s read; the exchange buffer is free
+    last_issued = last_issued < pt.ntiles ? next_tile(last_issued + G) : pt.ntiles;
+    if (tid == 0 && last_issued < pt.ntiles) {
+      fence_proxy_async_smem();
+      issue(last_issued, s);
+    }
+    float2* x1 = xb + col * kCS1;
+    float2* x2 = xb + col * kCS2;
+    pass1t<INV, !INV && HALF>(v, t, tw, x1, 64);
+    __syncthreads();
+    {
+      float2 u[8];
+      pass2t_load<INV>(u, t, x1, 64, tw);
+      __syncthreads();                     // X1 read: X2 overwrites the same buffer
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x2[c * 72 + 9 * q + g] = u[q];
+    }
+    __syncthreads();
+    pass3<INV>(c, g, x2, v);
+    if (col_ok) {
+      float2* out = a.out + bb * a.out_bs + o * a.out_os + (long long)(c0 + col) +
+                    (long long)(c + 8 * g) * a.out_ls;
+      const long long step = (long long)kM * a.out_ls;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        if (INV && HALF && h >= 4) continue;
+        const int p = c + 8 * g + kM * h;
+        if (p >= a.lout) continue;
+        float2 x = v[h];
+        if (INV) {
+          x = a.scale * x;
+          if (a.flags & EPI_CONJ) x = conjg(x);
+          if (a.flags & (EPI_SUB | EPI_ADD)) {
+            if (a.flags & EPI_CHI) x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
+            float2 w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + col) + (long long)p * a.out_ls];
+            if (a.flags & EPI_RSCALE) w = rs * w;
+            x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+          }
+        }
+        out[h * step] = x;
+      }
+    }
+    s = (s + 1 == NS) ? 0 : s + 1;
+    cur = next_tile(cur + G);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused z stage: one CTA of 256 threads per (k1, k2) mirror group, 64 threads
 // per mirror line (thread tid: line l = tid >> 6, slot t = tid & 63).  Each
 // thread carries the three Cartesian components of its line through the
@@ -202,7 +433,7 @@ __global__ void __launch_bounds__(512, 3) line_tp_kernel(const LineArgs<float> a
 // ---------------------------------------------------------------------------
 constexpr int kGS = 256 + 32 + 1;     // ghalf_slot(256) + 1
 constexpr int kLA = 72;               // X1 row stride of the fused layout
-constexpr size_t kFusedSmem = (size_t)(6 * kGS + 4 * kX2 + 4 * kX2) * sizeof(float2);
+constexpr size_t kFusedSmem = (size_t)(6 * kGS + 4 * kX2 + 4 * kX2 + kTwRows * kM) * sizeof(float2);
 
 template <bool STORED>
 __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float> a) {
@@ -211,6 +442,7 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
   const int tid = threadIdx.x, l = tid >> 6, t = tid & 63;
   float2* x1 = ghalf + 6 * kGS + l * kX2;
   float2* x2 = ghalf + 6 * kGS + 4 * kX2 + l * kX2;
+  float2* tw = ghalf + 6 * kGS + 8 * kX2;
   const int grp = a.g0 + blockIdx.x;
   const int k1 = grp / a.H2, k2 = grp % a.H2;
   const int nx = (k1 == 0 || 2 * k1 == a.P1) ? 1 : 2;
@@ -220,6 +452,7 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
   const int kx = ix ? a.P1 - k1 : k1, ky = iy ? a.P2 - k2 : k2;
   const long long line_off = ((long long)kx * a.P2 + ky) * a.n3;
   const int n3 = a.n3;
+  fill_twiddles(tw, a.roots, tid, 256);
   pdl_trigger();
   pdl_wait();
   if (a.prof != nullptr && grp == 0 && tid == 0) {
@@ -249,9 +482,14 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
         const int p = t + kM * m;
         v[m] = (m < 4 && valid && p < n3) ? line[p] : make_float2(0.f, 0.f);
       }
-      pass1<false, true>(v, t, a.roots, x1, kLA);
+      pass1t<false, true>(v, t, tw, x1, kLA);
       __syncthreads();
-      pass2<false>(c, t & 7, x1, kLA, x2, a.roots);
+      {
+        float2 u[8];
+        pass2t_load<false>(u, t, x1, kLA, tw);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x2[c * 72 + 9 * q + (t & 7)] = u[q];
+      }
       __syncthreads();
       pass3<false>(c, g, x2, s[comp]);
     }
@@ -285,9 +523,9 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       float2* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-      ipass3(c, g, s[comp], x2, a.roots);
+      ipass3t(t, s[comp], x2, tw);
       __syncthreads();
-      ipass2(c, t & 7, x2, x1, kLA, a.roots);
+      ipass2t(t, x2, x1, kLA, tw);
       __syncthreads();
       float2 v[8];
       ipass1(t, x1, kLA, v);
@@ -303,12 +541,53 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
 
 }  // namespace tp
 
+static int g_sms = 0;
+
+// the TMA-pipelined persistent form: input rows 256 or 512, strides of 16-byte
+// multiples, 16-byte aligned input
+static bool launch_line_tpp(LineArgs<float> a, bool half, cudaStream_t s) {
+  const int rows = a.lin;
+  if (rows != 256 && rows != 512) return false;
+  if (((uintptr_t)a.in & 15u) != 0 || a.in_os % 2 || a.in_ls % 2 || a.in_bs % 2) return false;
+  tp::PipeTiles pt;
+  pt.ncg = (a.ncol + tp::kLineCols - 1) / tp::kLineCols;
+  if ((long long)pt.ncg * a.nother * a.nbatch >= (1LL << 31)) return false;
+  pt.ntiles = pt.ncg * a.nother * a.nbatch;
+  pt.rows = rows;
+  pt.p_dim = a.in_ls < a.in_os ? 1 : 2;
+  const unsigned long long dp = (unsigned long long)rows, doth = (unsigned long long)a.nother;
+  const unsigned long long dims[4] = {(unsigned long long)a.ncol, pt.p_dim == 1 ? dp : doth,
+                                      pt.p_dim == 1 ? doth : dp, (unsigned long long)a.nbatch};
+  const unsigned long long strides[3] = {(unsigned long long)(pt.p_dim == 1 ? a.in_ls : a.in_os),
+                                         (unsigned long long)(pt.p_dim == 1 ? a.in_os : a.in_ls),
+                                         (unsigned long long)a.in_bs};
+  pt.nstage = rows == 256 ? 4 : 2;
+  const unsigned box_rows = rows < 256 ? rows : 256;
+  const unsigned box[4] = {(unsigned)tp::kLineCols, pt.p_dim == 1 ? box_rows : 1u,
+                           pt.p_dim == 1 ? 1u : box_rows, 1u};
+  CUtensorMap map;
+  if (encode_tensor_map_c64(&map, a.in, 4, dims, strides, box) != VIE_OK) return false;
+  if (g_sms == 0) g_sms = device_sms();
+  const long long grid = std::min<long long>(pt.ntiles, 2LL * g_sms);
+  a.prof = prof_bytes(a.prof_family);
+  ProfScope ps(a.prof_family, s);
+  const size_t smem = tp::pipe_smem(rows, pt.nstage);
+  if (a.inverse)
+    launch_pdl(half ? tp::line_tpp_kernel<true, true> : tp::line_tpp_kernel<true, false>,
+               dim3((unsigned)grid), dim3(512), smem, s, a, map, pt);
+  else
+    launch_pdl(half ? tp::line_tpp_kernel<false, true> : tp::line_tpp_kernel<false, false>,
+               dim3((unsigned)grid), dim3(512), smem, s, a, map, pt);
+  return true;
+}
+
 // x / y stage of a length-512 line (columns contiguous in memory)
 bool launch_line_tp(LineArgs<float> a, cudaStream_t s) {
   if (a.plan.N != tp::kN || a.in_cs != 1 || a.out_cs != 1) return false;
   if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
   if (a.nother > 65535 || a.nbatch > 65535) return false;
   const bool half = a.inverse ? (2 * a.lout == tp::kN) : (2 * a.lin == tp::kN);
+  if (launch_line_tpp(a, half, s)) return true;
   dim3 grid((a.ncol + tp::kLineCols - 1) / tp::kLineCols, a.nother, a.nbatch);
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
@@ -342,7 +621,46 @@ int tp_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
+  const int ps = (int)std::max(vie::tp::pipe_smem(256, 4), vie::tp::pipe_smem(512, 2));
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "length-512 kernel attributes");
+}
+
+// Host: tiled tensor map of 8-byte elements through the driver entry point
+// (looked up once; the library links only the runtime).
+int encode_tensor_map_c64(CUtensorMap* map, const void* base, int rank, const unsigned long long* dims,
+                          const unsigned long long* strides, const unsigned* box) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Encode>(p);
+    else
+      cudaGetLastError();
+    looked = true;
+  }
+  if (fn == nullptr || rank < 1 || rank > 5) return VIE_ERR_ARG;
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bd[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bd[i] = box[i];
+    es[i] = 1;
+    if (i > 0) gs[i - 1] = strides[i - 1] * 8ull;
+  }
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void*>(base), gd,
+                        gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? VIE_OK : VIE_ERR_ARG;
 }

@@ -152,6 +152,7 @@ template <typename T> struct LineArgs {
   int prof_family;                     // profiler family of this launch
   unsigned long long* prof;            // profiler byte counter (nullptr = off)
   unsigned long long prof_batch_bytes; // algorithmic bytes per active batch index
+  int* err;                            // device word set when a bounded wait gives up (or nullptr)
 };
 
 template <typename T> void launch_line_fft(const LineArgs<T>& a, cudaStream_t s);
@@ -229,6 +230,9 @@ struct vie_op {
   float2* roots32[3] = {};   double2* roots64[3] = {};
   // device copy of per-component metadata for the fused kernel
   void* meta = nullptr;
+  // device word that kernels with bounded waits set when a wait gives up
+  // (VIE_ERR_TIMEOUT, reported by vie_solve); zero otherwise
+  int* dev_err = nullptr;
   Workspace ws;
   int ws_batch = 0;
   Tuning tune;
