@@ -398,6 +398,19 @@ typedef struct vie_profile_entry {
 int vie_profile_start(unsigned mask);
 int vie_profile_stop(vie_profile_entry* out, int max_entries, int* count);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper).  The
+ * TMA-fed kernels wait on shared-memory barriers for their copies with a
+ * limit of one second of the device's global timer; a wait that runs out sets
+ * a device word that the next vie_solve synchronisation reports as
+ * VIE_ERR_TIMEOUT, and the kernel returns.  This call runs that wait alone in
+ * one thread: with arrive = 1 the barrier's arrival is made first and the
+ * call returns VIE_OK; with arrive = 0 nothing arrives, the wait gives up
+ * after `seconds` (0 < seconds <= 10) and the call returns VIE_ERR_TIMEOUT.
+ * Synchronises `stream`.
+ */
+int vie_selftest_bounded_wait(int arrive, double seconds, void* stream);
+
 /* Release `op` and everything it owns (NULL is allowed). */
 void vie_destroy(vie_op* op);
 

@@ -38,7 +38,7 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
            "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune",
-           "vie_solve_multi", "vie_tucker_cp", "vie_cp_export")
+           "vie_solve_multi", "vie_tucker_cp", "vie_cp_export", "vie_selftest_bounded_wait")
 
 
 class VieError(RuntimeError):
@@ -117,6 +117,7 @@ def _load():
         "vie_profile_start": [ctypes.c_uint],
         "vie_profile_stop": [ctypes.POINTER(ProfileEntry), ci, ctypes.POINTER(ci)],
         "vie_status_string": [ci],
+        "vie_selftest_bounded_wait": [ci, cd, vp],
         "vie_last_error": [],
     }
     for name, args in sig.items():

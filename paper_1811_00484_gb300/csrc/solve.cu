@@ -988,6 +988,20 @@ static void harvest_graph(SolverState* st) {
   st->graph_pending = false;
 }
 
+// A kernel whose bounded wait gave up has set the operator's error word: report
+// it (and clear it) after a synchronisation.
+static int check_device_error(const vie_op* op, cudaStream_t s) {
+  int h = 0;
+  VIE_CUDA(cudaMemcpyAsync(&h, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+  if (h != 0) {
+    VIE_CUDA(cudaMemsetAsync(op->dev_err, 0, sizeof(int), s));
+    set_error("a bounded device wait gave up (an asynchronous copy did not complete)");
+    return VIE_ERR_TIMEOUT;
+  }
+  return VIE_OK;
+}
+
 // FP32 GMRES on r32 (unit-norm rows) to relative tolerance `tol` for the RHS in `want`.
 static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint, double tol,
                        int max_outer, int passes, bool use_graph, const std::vector<int>& want,
@@ -1012,6 +1026,7 @@ static int inner_gmres(const vie_op* op, SolverState* st, int path, int adjoint,
     VIE_CUDA(cudaMemcpyAsync(act.data(), st->active, B * sizeof(int), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaStreamSynchronize(s));
     harvest_graph(st);
+    VIE_TRY(check_device_error(op, s));
     int nact = 0;
     for (int b = 0; b < B; ++b) nact += act[b];
     if (nact == 0) return VIE_OK;
@@ -1116,9 +1131,13 @@ static int solve_on(vie_op* op, SolverState* st, const void* chi, const void* rh
     VIE_CUDA(cudaMemcpyAsync(rn.data(), st->rnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaMemcpyAsync(bn.data(), st->bnorm, B * sizeof(double), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaStreamSynchronize(s));
+    VIE_TRY(check_device_error(op, s));
     double worst = 0.0;
     bool finite = true;
     for (int b = 0; b < B; ++b) {
+      // a non-finite norm (NaN or Inf in the inputs or the iterate) is an error,
+      // never a zero right-hand side
+      if (!std::isfinite(rn[b]) || !std::isfinite(bn[b])) finite = false;
       const double rel = bn[b] > 0.0 ? rn[b] / bn[b] : 0.0;
       if (!std::isfinite(rel)) finite = false;
       want[b] = rel > o->tol ? 1 : 0;

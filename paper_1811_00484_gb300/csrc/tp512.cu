@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(512, 3) line_tp_kernel(const LineArgs<float> a
 // ---------------------------------------------------------------------------
 constexpr size_t kPipeX = (size_t)kLineCols * kCS2 * sizeof(float2);   // X1 / X2 (37 KB)
 constexpr size_t kTwBytes = (size_t)kTwRows * kM * sizeof(float2);       // 11 KB
-constexpr unsigned kWaitPolls = 1u << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;     // 1 s per bounded wait
 constexpr int kMaxStages = 4;
 
 struct PipeTiles {
@@ -343,10 +343,10 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
   int s = 0;
   unsigned phase_bits = 0;                        // bit q: parity of the next wait on stage q
   while (cur < pt.ntiles) {
-    const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, kWaitPolls);
+    const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, kWaitNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0 && a.err != nullptr) atomicExch(a.err, VIE_ERR_TIMEOUT);
-      for (int q = 0; q < NS; ++q) mbar_wait_bounded(&bar[q], (phase_bits >> q) & 1u, kWaitPolls);
+      for (int q = 0; q < NS; ++q) mbar_wait_bounded(&bar[q], (phase_bits >> q) & 1u, kWaitNs);
       return;
     }
     phase_bits ^= 1u << s;
@@ -663,4 +663,44 @@ int encode_tensor_map_c64(CUtensorMap* map, const void* base, int rank, const un
                         gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? VIE_OK : VIE_ERR_ARG;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread waits on a shared-memory mbarrier
+// for at most `limit_ns`; with arrive = 1 the barrier's single arrival is
+// made first (the wait completes), with arrive = 0 nothing arrives and the
+// wait must give up.  status: 1 completed, 2 gave up.
+// ---------------------------------------------------------------------------
+namespace vie {
+__global__ void bounded_wait_selftest_kernel(int arrive, unsigned long long limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  *status = mbar_wait_bounded(&bar, 0, limit_ns) ? 1 : 2;
+}
+}  // namespace vie
+
+extern "C" int vie_selftest_bounded_wait(int arrive, double seconds, void* stream) {
+  clear_error();
+  if (seconds <= 0.0 || seconds > 10.0) {
+    set_error("wait limit %g s outside (0, 10]", seconds);
+    return VIE_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  VIE_CUDA(cudaMalloc(&d, sizeof(int)));
+  int h = 0;
+  vie::bounded_wait_selftest_kernel<<<1, 1, 0, s>>>(arrive ? 1 : 0,
+                                                      (unsigned long long)(seconds * 1e9), d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(e, "bounded-wait self-test");
+  if (h == 2) {
+    set_error("the bounded wait gave up after %g s", seconds);
+    return VIE_ERR_TIMEOUT;
+  }
+  return h == 1 ? VIE_OK : VIE_ERR_CUDA;
 }

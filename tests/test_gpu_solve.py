@@ -174,6 +174,41 @@ def test_no_convergence_is_reported():
         op.solve(dev(wl.chi), dev(wl.einc), tol=1e-12, max_refine=1, max_outer=1, restart=2)
 
 
+@pytest.mark.parametrize("where", ["chi", "einc"])
+def test_non_finite_input_is_reported(where):
+    """A NaN placed in the contrast or the incident field on the host makes the
+    first FP64 residual non-finite: the solve stops with VIE_ERR_NUMERIC."""
+    wl, T, Ghat, Gt, op = case((8, 6, 10), tol_svd=1e-8, seed=3)
+    chi, einc = wl.chi.copy(), wl.einc.copy()
+    if where == "chi":
+        chi[4, 3, 5] = np.nan
+    else:
+        einc[0, 1, 2, 2, 2] = np.nan
+    with pytest.raises(vie.VieError) as e:
+        op.solve(dev(chi), dev(einc), tol=1e-8)
+    assert e.value.status == 5 and "non-finite" in str(e.value)
+    # the operator is still usable afterwards
+    w, info = op.solve(dev(wl.chi), dev(wl.einc), tol=1e-6)
+    assert info["converged"]
+
+
+def test_bounded_device_wait_gives_up_and_reports_timeout():
+    """The shared-memory barrier wait of the TMA-fed kernels, run alone: it
+    completes when the arrival is made, and gives up after its limit (reported
+    as VIE_ERR_TIMEOUT) when nothing arrives; the context stays usable."""
+    import ctypes
+    import time
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert vie.lib.vie_selftest_bounded_wait(1, 0.05, stream) == 0
+    t0 = time.perf_counter()
+    assert vie.lib.vie_selftest_bounded_wait(0, 0.05, stream) == 6
+    assert time.perf_counter() - t0 < 5.0
+    assert "gave up" in vie.lib.vie_last_error().decode()
+    assert vie.lib.vie_selftest_bounded_wait(0, 0.0, stream) == 1
+    x = torch.ones(8, device="cuda")
+    assert float((x * 2).sum()) == 16.0
+
+
 def test_autograd_gradient_matches_oracle_and_finite_differences():
     wl, T, Ghat, Gt, op = case((6, 6, 6), tol_svd=1e-10, seed=9)
     rng = np.random.default_rng(3)
