@@ -379,7 +379,8 @@ int vie_incident_dipole(const vie_op* op, const double* sources, int B, void* ou
  * vie_profile_start(mask) and vie_profile_stop() every launch of the kernel
  * families selected by `mask` (bit f = family f in the order line_x, line_y,
  * fused_tucker, fused_stored, line_iy, line_ix, tucker_rebuild, arnoldi_dots,
- * arnoldi_update, arnoldi_small, fp64_vector, setup; ~0u = all) is
+ * arnoldi_update, arnoldi_small, fp64_vector, setup, matvec_fp64 (every stage
+ * of the FP64 refinement matvecs); ~0u = all) is
  * bracketed by CUDA events on the stream it runs on
  * (inside CUDA graphs as event nodes read after each replay), and kernels
  * add the algorithmic bytes they move for active right-hand sides to a

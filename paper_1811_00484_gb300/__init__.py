@@ -356,7 +356,7 @@ class Operator:
 
 PROFILE_FAMILIES = ("line_x", "line_y", "fused_tucker", "fused_stored", "line_iy", "line_ix",
                     "tucker_rebuild", "arnoldi_dots", "arnoldi_update", "arnoldi_small", "fp64_vector",
-                    "setup")
+                    "setup", "matvec_fp64")
 
 
 def _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph, refine, orth):

@@ -655,7 +655,7 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   const size_t smem = fused_warp_smem(R, a.H3, a.r2max, a.r3max);
   const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
   a.prof = prof_bytes(fam);
-  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(float2);
+  a.prof_rhs_bytes = 12ull * a.comp_stride * sizeof(float2);     // 48 B per padded voxel
   a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(float2) : 0ull;
   // the four-step kernel when R is even (and, on the Tucker path, the half
   // fibres come from the rebuild scratch)
@@ -740,9 +740,9 @@ static int launch_fused_impl(FusedArgs<T> a, cudaStream_t s) {
     return VIE_ERR_ARG;
   }
   a.lines_per_round = LR;
-  const int fam = STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER;
-  a.prof = prof_bytes(fam);
-  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(cx<T>);       // 3 components read + written
+  const int fam = sizeof(T) == 8 ? PF_MATVEC64 : (STORED ? PF_FUSED_STORED : PF_FUSED_TUCKER);
+  a.prof = sizeof(T) == 8 ? nullptr : prof_bytes(fam);
+  a.prof_rhs_bytes = 12ull * a.comp_stride * sizeof(cx<T>);      // 48 B per padded voxel
   a.prof_launch_bytes = STORED ? 6ull * a.spec_stride * sizeof(cx<T>) : 0ull;
   ProfScope ps(fam, s);
   fused_z_kernel<T, STORED><<<a.H1 * a.H2, 256, fused_smem(a, LR), s>>>(a);
@@ -821,7 +821,10 @@ vie::FusedArgs<T> make_fused_args(const vie_op* op, cx<T>* data, int B, bool sto
   a.lines_per_round = 4;
   const int fam = stored ? PF_FUSED_STORED : PF_FUSED_TUCKER;
   a.prof = prof_bytes(fam);
-  a.prof_rhs_bytes = 6ull * a.comp_stride * sizeof(cx<T>);
+  // algorithmic bytes of the voxel-wise product (read J^, write Y^): 48 B per
+  // padded voxel and right-hand side; the fused kernel itself moves half of
+  // that (n3 of P3 z-points in and out), the zero padding never leaving chip
+  a.prof_rhs_bytes = 12ull * a.comp_stride * sizeof(cx<T>);
   a.prof_launch_bytes = stored ? 6ull * a.spec_stride * sizeof(cx<T>) : 0ull;
   (void)stored;
   return a;

@@ -158,6 +158,12 @@ LineStages<T> make_line_stages(const vie_op* op, void* ws, const cx<T>* in, cx<T
     st.s[i].rscale = rscale;
     st.s[i].rscale_stride = rscale_stride;
     st.s[i].err = op->dev_err;
+    // the FP64 stages (refinement residuals) form one family of their own: they
+    // are bound by FP64 arithmetic, and count no algorithmic bytes
+    if constexpr (sizeof(T) == 8) {
+      st.s[i].prof_family = PF_MATVEC64;
+      st.s[i].prof_batch_bytes = 0;
+    }
   }
   return st;
 }

@@ -36,7 +36,8 @@ thread_local std::vector<Pair>* t_capture_sink = nullptr;
 
 const char* kNames[VIE_PROF_FAMILIES] = {"line_x",    "line_y",   "fused_tucker", "fused_stored",
                                          "line_iy",   "line_ix",  "tucker_rebuild", "arnoldi_dots",
-                                         "arnoldi_update", "arnoldi_small", "fp64_vector", "setup"};
+                                         "arnoldi_update", "arnoldi_small", "fp64_vector", "setup",
+                                         "matvec_fp64"};
 
 void harvest(std::vector<Pair>& v, Profiler& p, bool recycle) {
   for (Pair& q : v) {

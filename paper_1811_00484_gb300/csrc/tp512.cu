@@ -436,7 +436,7 @@ constexpr int kLA = 72;               // X1 row stride of the fused layout
 constexpr size_t kFusedSmem = (size_t)(6 * kGS + 4 * kX2 + 4 * kX2 + kTwRows * kM) * sizeof(float2);
 
 template <bool STORED>
-__global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float> a) {
+__global__ void __launch_bounds__(256, STORED ? 2 : 3) fused_tp_kernel(const FusedArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* ghalf = reinterpret_cast<float2*>(smem_raw);   // [6][kGS]
   const int tid = threadIdx.x, l = tid >> 6, t = tid & 63;
@@ -511,31 +511,34 @@ __global__ void __launch_bounds__(256, 2) fused_tp_kernel(const FusedArgs<float>
 #pragma unroll
         for (int q = 0; q < 6; ++q) G[q] = gp[q * kGS];
       }
-      const float2 jx = sx * s[0][h], jy = sy * s[1][h], jz = sz * s[2][h];
-      const float2 yx = cmadd(G[0], jx, cmadd(G[1], jy, G[2] * jz));
-      const float2 yy = cmadd(G[1], jx, cmadd(G[3], jy, G[4] * jz));
-      const float2 yz = cmadd(G[2], jx, cmadd(G[4], jy, G[5] * jz));
-      s[0][h] = sx * yx;
-      s[1][h] = sy * yy;
-      s[2][h] = sz * yz;
+      // D G D with the mirror signs folded into the off-diagonal entries
+      const float sxy = sx * sy, sxz = sx * sz, syz = sy * sz;
+      const float2 gxy = sxy * G[1], gxz = sxz * G[2], gyz = syz * G[4];
+      const float2 jx = s[0][h], jy = s[1][h], jz = s[2][h];
+      s[0][h] = cmadd(G[0], jx, cmadd(gxy, jy, gxz * jz));
+      s[1][h] = cmadd(gxy, jx, cmadd(G[3], jy, gyz * jz));
+      s[2][h] = cmadd(gxz, jx, cmadd(gyz, jy, G[5] * jz));
     }
-    __syncthreads();                 // every thread is done with X2 of the forward passes
+    // inverse passes: the first writes X1 (in the X2 layout), which the forward
+    // passes last read before the barrier that preceded pass 3, the second
+    // reads X1 and writes X2 (layout of X1), the third reads X2
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       float2* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-      ipass3t(t, s[comp], x2, tw);
+      ipass3t(t, s[comp], x1, tw);
       __syncthreads();
-      ipass2t(t, x2, x1, kLA, tw);
+      ipass2t(t, x1, x2, kLA, tw);
       __syncthreads();
       float2 v[8];
-      ipass1(t, x1, kLA, v);
+      ipass1(t, x2, kLA, v);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int p = t + kM * m;
         if (valid && p < n3) line[p] = v[m];
       }
     }
-    __syncthreads();                 // X1 is rewritten by the next right-hand side
+    // the next right-hand side's pass 1 writes X1, last read by the inverse pass
+    // 2 above before the barrier that preceded the inverse pass 1
   }
 }
 

@@ -106,7 +106,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // ---------------------------------------------------------------------------
 enum {
   PF_LINE_X = 0, PF_LINE_Y, PF_FUSED_TUCKER, PF_FUSED_STORED, PF_LINE_IY, PF_LINE_IX, PF_REBUILD,
-  PF_DOTS, PF_UPDATE, PF_SMALL, PF_FP64, PF_SETUP, VIE_PROF_FAMILIES
+  PF_DOTS, PF_UPDATE, PF_SMALL, PF_FP64, PF_SETUP, PF_MATVEC64, VIE_PROF_FAMILIES
 };
 struct ProfEventPair {
   cudaEvent_t a, b;
