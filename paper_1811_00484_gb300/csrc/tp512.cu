@@ -285,7 +285,17 @@ __host__ __device__ constexpr size_t pipe_smem(int rows, int nstage) {
          1024;
 }
 
-template <bool INV, bool HALF>
+// Position of a tile (column group, other index, batch index) of the CTA's
+// sequence blockIdx.x, blockIdx.x + G, ...: stepped by G with carries, no
+// divisions.
+struct TilePos {
+  int cg, o, bb;
+};
+struct TileStep {
+  int cg, o, bb;        // G split into the three digits (cg fastest)
+};
+
+template <bool INV, bool HALF, bool FLAGS>
 __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> a,
                                                         const __grid_constant__ CUtensorMap map,
                                                         const PipeTiles pt) {
@@ -307,42 +317,66 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
   __syncthreads();
   pdl_trigger();
   pdl_wait();
-  const int per_bb = pt.ncg * a.nother;
-  const int G = gridDim.x;
-  auto next_tile = [&](int from) {
-    if (a.active == nullptr) return from < pt.ntiles ? from : pt.ntiles;
-    for (int q = from; q < pt.ntiles; q += G)
-      if (a.active[(q / per_bb) / a.batch_per_rhs] != 0) return q;
-    return pt.ntiles;
+  const int ncg = pt.ncg, nother = a.nother, nbatch = a.nbatch;
+  TileStep st;
+  {
+    const int G = gridDim.x;
+    st.cg = G % ncg;
+    const int r = G / ncg;
+    st.o = r % nother;
+    st.bb = r / nother;
+  }
+  auto advance = [&](TilePos& q) {
+    q.cg += st.cg;
+    int carry = q.cg >= ncg;
+    if (carry) q.cg -= ncg;
+    q.o += st.o + carry;
+    carry = q.o >= nother;
+    if (carry) q.o -= nother;
+    q.bb += st.bb + carry;
+  };
+  // the next tile at or after q (in steps of G) whose right-hand side is active
+  auto settle = [&](TilePos& q) {
+    if (a.active == nullptr) return;
+    while (q.bb < nbatch && a.active[q.bb / 3] == 0) advance(q);
   };
   const int box_rows = pt.rows < 256 ? pt.rows : 256;
-  auto issue = [&](int tile, int s) {
-    const int cg = tile % pt.ncg, rest = tile / pt.ncg;
-    const int o = rest % a.nother, bb = rest / a.nother;
+  auto issue = [&](const TilePos& q, int s) {
     mbar_arrive_expect_tx(&bar[s], (unsigned)sbytes);
     for (int p0 = 0; p0 < pt.rows; p0 += box_rows) {
-      const int c1 = pt.p_dim == 1 ? p0 : o, c2 = pt.p_dim == 1 ? o : p0;
-      tma_load_4d(stage(s) + p0 * kLineCols, &map, cg * kLineCols, c1, c2, bb, &bar[s]);
+      const int c1 = pt.p_dim == 1 ? p0 : q.o, c2 = pt.p_dim == 1 ? q.o : p0;
+      tma_load_4d(stage(s) + p0 * kLineCols, &map, q.cg * kLineCols, c1, c2, q.bb, &bar[s]);
     }
   };
-  // the ring holds the tile cur and the next NS - 1 ones (last_issued is the newest)
-  int cur = next_tile(blockIdx.x);
-  int last_issued = cur;
-  if (tid == 0 && cur < pt.ntiles) issue(cur, 0);
+  TilePos cur;
+  {
+    const int b0 = blockIdx.x;
+    cur.cg = b0 % ncg;
+    const int r = b0 / ncg;
+    cur.o = r % nother;
+    cur.bb = r / nother;
+  }
+  settle(cur);
+  // the ring holds the tile cur and the next NS - 1 ones (ahead is the newest)
+  TilePos ahead = cur;
+  if (tid == 0 && cur.bb < nbatch) issue(cur, 0);
   for (int q = 1; q < NS; ++q) {
-    last_issued = last_issued < pt.ntiles ? next_tile(last_issued + G) : pt.ntiles;
-    if (tid == 0 && last_issued < pt.ntiles) issue(last_issued, q);
+    if (ahead.bb < nbatch) {
+      advance(ahead);
+      settle(ahead);
+    }
+    if (tid == 0 && ahead.bb < nbatch) issue(ahead, q);
   }
   if (a.prof != nullptr && blockIdx.x == 0 && tid == 0) {
     unsigned long long nb = 0;
-    for (int bb = 0; bb < a.nbatch; ++bb)
-      nb += (a.active == nullptr || a.active[bb / a.batch_per_rhs]) ? 1 : 0;
+    for (int bb = 0; bb < nbatch; ++bb) nb += (a.active == nullptr || a.active[bb / 3]) ? 1 : 0;
     atomicAdd(a.prof, nb * a.prof_batch_bytes);
   }
   const int c = t >> 3, g = t & 7;
+  const long long out_step = (long long)kM * a.out_ls;
   int s = 0;
   unsigned phase_bits = 0;                        // bit q: parity of the next wait on stage q
-  while (cur < pt.ntiles) {
+  while (cur.bb < nbatch) {
     const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, kWaitNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0 && a.err != nullptr) atomicExch(a.err, VIE_ERR_TIMEOUT);
@@ -350,22 +384,21 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
       return;
     }
     phase_bits ^= 1u << s;
-    const int cg = cur % pt.ncg, rest = cur / pt.ncg;
-    const int o = rest % a.nother, bb = rest / a.nother;
-    const int c0 = cg * kLineCols;
+    const int o = cur.o, bb = cur.bb;
+    const int c0 = cur.cg * kLineCols;
     const bool col_ok = c0 + col < a.ncol;
-    const float rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
-                         ? (float)a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
-                         : 1.f;
+    float rs = 1.f;
+    if (FLAGS && (a.flags & (PRO_RSCALE | EPI_RSCALE)))
+      rs = (float)a.rscale[(long long)(bb / 3) * a.rscale_stride];
     const float2* S = stage(s) + col;
     float2 v[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int p = t + kM * b;
       float2 x = make_float2(0.f, 0.f);
-      if ((INV || !HALF || b < 4) && p < pt.rows) {
+      if (INV || !HALF || b < 4) {
         x = S[p * kLineCols];
-        if (!INV) {
+        if (FLAGS && !INV) {
           if (a.flags & PRO_RSCALE) x = rs * x;
           if (a.flags & PRO_CONJ) x = conjg(x);
           if ((a.flags & PRO_CHI) && col_ok)
@@ -375,10 +408,13 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
       v[b] = x;
     }
     __syncthreads();                       // stage s read; the exchange buffer is free
-    last_issued = last_issued < pt.ntiles ? next_tile(last_issued + G) : pt.ntiles;
-    if (tid == 0 && last_issued < pt.ntiles) {
+    if (ahead.bb < nbatch) {
+      advance(ahead);
+      settle(ahead);
+    }
+    if (tid == 0 && ahead.bb < nbatch) {
       fence_proxy_async_smem();
-      issue(last_issued, s);
+      issue(ahead, s);
     }
     float2* x1 = xb + col * kCS1;
     float2* x2 = xb + col * kCS2;
@@ -396,28 +432,31 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
     if (col_ok) {
       float2* out = a.out + bb * a.out_bs + o * a.out_os + (long long)(c0 + col) +
                     (long long)(c + 8 * g) * a.out_ls;
-      const long long step = (long long)kM * a.out_ls;
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
         if (INV && HALF && h >= 4) continue;
-        const int p = c + 8 * g + kM * h;
-        if (p >= a.lout) continue;
         float2 x = v[h];
         if (INV) {
           x = a.scale * x;
-          if (a.flags & EPI_CONJ) x = conjg(x);
-          if (a.flags & (EPI_SUB | EPI_ADD)) {
-            if (a.flags & EPI_CHI) x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
-            float2 w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + col) + (long long)p * a.out_ls];
-            if (a.flags & EPI_RSCALE) w = rs * w;
-            x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+          if (FLAGS) {
+            const int p = c + 8 * g + kM * h;
+            if (a.flags & EPI_CONJ) x = conjg(x);
+            if (a.flags & (EPI_SUB | EPI_ADD)) {
+              if (a.flags & EPI_CHI)
+                x = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * x;
+              float2 w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + col) +
+                                  (long long)p * a.out_ls];
+              if (a.flags & EPI_RSCALE) w = rs * w;
+              x = (a.flags & EPI_SUB) ? (w - x) : (w + x);
+            }
           }
         }
-        out[h * step] = x;
+        out[h * out_step] = x;
       }
     }
     s = (s + 1 == NS) ? 0 : s + 1;
-    cur = next_tile(cur + G);
+    advance(cur);
+    settle(cur);
   }
 }
 
@@ -551,6 +590,12 @@ static int g_sms = 0;
 static bool launch_line_tpp(LineArgs<float> a, bool half, cudaStream_t s) {
   const int rows = a.lin;
   if (rows != 256 && rows != 512) return false;
+  // every tile's rows are loaded and, inverse and halved, its first 256 outputs
+  // stored: the kernel relies on lin = N (inverse) or N / 2 (forward halved)
+  // and lout = N / 2 (inverse halved) or N (forward)
+  if (a.inverse ? (rows != 512 || a.lout != (half ? 256 : 512)) : (a.lout != 512 || rows != (half ? 256 : 512)))
+    return false;
+  if (a.batch_per_rhs != 3) return false;
   if (((uintptr_t)a.in & 15u) != 0 || a.in_os % 2 || a.in_ls % 2 || a.in_bs % 2) return false;
   tp::PipeTiles pt;
   pt.ncg = (a.ncol + tp::kLineCols - 1) / tp::kLineCols;
@@ -575,12 +620,14 @@ static bool launch_line_tpp(LineArgs<float> a, bool half, cudaStream_t s) {
   a.prof = prof_bytes(a.prof_family);
   ProfScope ps(a.prof_family, s);
   const size_t smem = tp::pipe_smem(rows, pt.nstage);
-  if (a.inverse)
-    launch_pdl(half ? tp::line_tpp_kernel<true, true> : tp::line_tpp_kernel<true, false>,
-               dim3((unsigned)grid), dim3(512), smem, s, a, map, pt);
-  else
-    launch_pdl(half ? tp::line_tpp_kernel<false, true> : tp::line_tpp_kernel<false, false>,
-               dim3((unsigned)grid), dim3(512), smem, s, a, map, pt);
+  using K = void (*)(LineArgs<float>, CUtensorMap, tp::PipeTiles);
+  static const K kernels[2][2][2] = {
+      {{tp::line_tpp_kernel<false, false, false>, tp::line_tpp_kernel<false, false, true>},
+       {tp::line_tpp_kernel<false, true, false>, tp::line_tpp_kernel<false, true, true>}},
+      {{tp::line_tpp_kernel<true, false, false>, tp::line_tpp_kernel<true, false, true>},
+       {tp::line_tpp_kernel<true, true, false>, tp::line_tpp_kernel<true, true, true>}}};
+  const K k = kernels[a.inverse ? 1 : 0][half ? 1 : 0][a.flags != 0 ? 1 : 0];
+  launch_pdl(k, dim3((unsigned)grid), dim3(512), smem, s, a, map, pt);
   return true;
 }
 
@@ -625,10 +672,13 @@ int tp_init_attributes() {
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tp_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ls);
   const int ps = (int)std::max(vie::tp::pipe_smem(256, 4), vie::tp::pipe_smem(512, 2));
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
-  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+#define VIE_TPP_ATTR(I, H, F) \
+  e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::line_tpp_kernel<I, H, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)
+  VIE_TPP_ATTR(false, false, false); VIE_TPP_ATTR(false, false, true);
+  VIE_TPP_ATTR(false, true, false); VIE_TPP_ATTR(false, true, true);
+  VIE_TPP_ATTR(true, false, false); VIE_TPP_ATTR(true, false, true);
+  VIE_TPP_ATTR(true, true, false); VIE_TPP_ATTR(true, true, true);
+#undef VIE_TPP_ATTR
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
   e = e != cudaSuccess ? e : cudaFuncSetAttribute(vie::tp::fused_tp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "length-512 kernel attributes");
