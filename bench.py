@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--n", type=int, default=64, help="grid edge (default: the 64^3 solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-n64", action="store_true", help="headline: skip the 64^3 solve summary")
+    p.add_argument("--only-steps", action="store_true",
+                   help="headline: warm-up and timed steps only (a short command for profilers; "
+                        "the timed steps run inside the NVTX range timed_steps)")
     p.add_argument("--no-batched", action="store_true", help="skip the 96^3 16-RHS solve")
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
     p.add_argument("--mode", default="headline",
@@ -70,6 +73,7 @@ def parse():
     p.add_argument("--family", help="kernel family of --record-traffic (e.g. fused_tucker)")
     p.add_argument("--kernel", default="", help="--record-traffic: regex on the kernel name")
     p.add_argument("--capture", default="", help="--record-traffic: the ncu command, for the record")
+    p.add_argument("--workload", default="", help="--record-traffic: the captured launches, for the record")
     return p.parse_args()
 
 
@@ -135,14 +139,15 @@ def record_traffic(args):
         raise SystemExit("no dram__bytes rows in " + args.record_traffic)
     table = traffic_rows()
     table[args.family] = [args.family, " ".join(sorted(names)), sources_digest(), str(len(per)),
-                          f"{sum(per.values()) / len(per):.0f}", "64^3 solve, every launch of one solve",
+                          f"{sum(per.values()) / len(per):.0f}", args.workload.replace("|", "/"),
                           args.capture.replace("|", "/")]
     with open(TRAFFIC_FILE, "w") as fh:
         fh.write("# DRAM traffic of the roofline kernel families\n\n"
                  "Written by `bench.py --record-traffic` from ncu captures of `dram__bytes_read.sum` + "
-                 "`dram__bytes_write.sum` (one pass per launch) over every launch of one bench solve. "
-                 "`sources` is a digest of the library sources at capture time: `bench.py` reports a "
-                 "row's traffic only while the sources still match it, and null otherwise.\n\n")
+                 "`dram__bytes_write.sum` (one pass per launch) of a few launches of each family in the "
+                 "bench's own launch shape. `sources` is a digest of the library sources at capture time: "
+                 "`bench.py` reports a row's traffic only while the sources still match it, and null "
+                 "otherwise.\n\n")
         fh.write(TRAFFIC_HEADER)
         for k in sorted(table):
             fh.write("| " + " | ".join(table[k]) + " |\n")
@@ -413,14 +418,25 @@ def run_headline(args):
         op.solve(chi, einc, out=w, **step_kw)
     op.solve(chi, einc, path="uncompressed", out=w, **step_kw)
     # one step with every kernel family instrumented: the breakdown
-    vie.profile_start()
-    timed_steps("tucker", 1, chi, einc)
-    kern = vie.profile_stop()
-    dom = max((k for k in kern if kern[k]["bytes"] > 0), key=lambda k: kern[k]["ms"])
+    kern, dom = {}, None
+    if not args.only_steps:
+        vie.profile_start()
+        timed_steps("tucker", 1, chi, einc)
+        kern = vie.profile_stop()
+        dom = max((k for k in kern if kern[k]["bytes"] > 0), key=lambda k: kern[k]["ms"])
     # timed region (the headline): no instrumentation inside the library
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         t_tucker, mv_tucker = timed_steps("tucker", args.steps, chi, einc)
+        torch.cuda.nvtx.range_pop()
     clocks = clk.summary()
+    if args.only_steps:
+        if rank == 0:
+            print(json.dumps({"mode": "only-steps", "metric": METRIC, "steps": args.steps,
+                              "ms_per_step": 1e3 * t_tucker / args.steps,
+                              "value": mv_tucker / t_tucker, "unit": UNIT, "clocks": clocks}))
+        op.close()
+        return
     k_unc = min(args.steps, 5)
     t_unc, mv_unc = timed_steps("uncompressed", k_unc, chi, einc)
     # the roofline kernel's launches timed with CUDA events on their stream
@@ -553,11 +569,14 @@ def run_headline(args):
                         "instrumented); the timed steps run without instrumentation",
         "gpu_launches": int(sum(v["launches"] for v in kern.values())) * args.steps,
     }
+    # the 64^3 solve after the headline operator and its buffers are released
+    op.close()
+    del w, einc, chi, chi_h, einc_h, w_h
+    torch.cuda.empty_cache()
     if rank == 0 and not args.no_n64:
         line["n64"] = solve64_summary(args)
     if rank == 0:
         print(json.dumps(line))
-    op.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -363,7 +363,7 @@ def _solve_opts(tol, restart, max_outer, inner_tol, max_refine, path, use_graph,
     if inner_tol is None:
         # the first inner solve aims below the target, so that FP32 rounding of its
         # residual estimate does not cost a second refinement step
-        inner_tol = max(0.5 * tol, 1e-7) if refine else tol
+        inner_tol = max(0.5 * tol, 5e-6) if refine else tol
     return SolveOpts(float(tol), int(restart), int(max_outer), float(inner_tol), int(max_refine),
                      PATHS[path], int(bool(use_graph)), int(bool(refine)), int(orth))
 
