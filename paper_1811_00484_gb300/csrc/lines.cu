@@ -203,6 +203,8 @@ template <typename T>
 void launch_line_fft(const LineArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     if (launch_warp(a, s)) return;
+  } else {
+    if (a.plan.N == 512 && launch_line_tp64(a, s)) return;
   }
   const int N = a.plan.N;
   auto bytes = [&](int tw) { return (size_t)(2 * N * tw + N) * sizeof(cx<T>); };

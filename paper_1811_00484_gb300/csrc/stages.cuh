@@ -719,6 +719,7 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
 
 // Length-512 kernels (tp512.cu): x / y line stages and the fused z stage
 bool launch_line_tp(LineArgs<float> a, cudaStream_t s);
+bool launch_line_tp64(LineArgs<double> a, cudaStream_t s);
 bool fused_tp_supported(const FusedArgs<float>& a, bool stored);
 void launch_fused_tp(const FusedArgs<float>& a, int groups, bool stored, cudaStream_t s);
 

@@ -34,24 +34,31 @@ constexpr int kN = 512;
 constexpr int kM = 64;            // threads per line
 constexpr int kX2 = 576;          // 8 x 72 per line
 
-__device__ __forceinline__ float2 root(const float2* roots, int e, bool inv) {
-  const float2 w = __ldg(roots + e);
+template <typename C>
+__device__ __forceinline__ C root(const C* roots, int e, bool inv) {
+  const C w = __ldg(roots + e);
   return inv ? conjg(w) : w;
 }
 
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
 // DFT-8 of x[0..3] with x[4..7] = 0: X[2k] = DFT4(x)[k], X[2k+1] = DFT4(x_n w8^n)[k]
-__device__ __forceinline__ void dft8_half_in(float2* v, bool inv) {
-  const float r = 0.70710678118654752440f;
-  float2 e0 = v[0], e1 = v[1], e2 = v[2], e3 = v[3];
-  float2 o0 = v[0], o1, o2, o3;
+template <typename C>
+__device__ __forceinline__ void dft8_half_in(C* v, bool inv) {
+  using T = typename RealOf<C>::type;
+  const T r = (T)0.70710678118654752440;
+  C e0 = v[0], e1 = v[1], e2 = v[2], e3 = v[3];
+  C o0 = v[0], o1, o2, o3;
   if (!inv) {
-    o1 = make_float2(r * (v[1].x + v[1].y), r * (v[1].y - v[1].x));
+    o1 = mk(r * (v[1].x + v[1].y), r * (v[1].y - v[1].x));
     o2 = mul_mi(v[2]);
-    o3 = make_float2(r * (v[3].y - v[3].x), -r * (v[3].x + v[3].y));
+    o3 = mk(r * (v[3].y - v[3].x), -r * (v[3].x + v[3].y));
   } else {
-    o1 = make_float2(r * (v[1].x - v[1].y), r * (v[1].x + v[1].y));
+    o1 = mk(r * (v[1].x - v[1].y), r * (v[1].x + v[1].y));
     o2 = mul_i(v[2]);
-    o3 = make_float2(-r * (v[3].x + v[3].y), r * (v[3].x - v[3].y));
+    o3 = mk(-r * (v[3].x + v[3].y), r * (v[3].x - v[3].y));
   }
   dft4(e0, e1, e2, e3, inv);
   dft4(o0, o1, o2, o3, inv);
@@ -60,9 +67,9 @@ __device__ __forceinline__ void dft8_half_in(float2* v, bool inv) {
 }
 
 // pass 1 in thread a: v[b] = x[a + 64 b]  ->  X1[c][a]
-template <bool INV, bool HALF_IN>
-__device__ __forceinline__ void pass1(float2 (&v)[8], int a, const float2* roots, float2* x1, int la) {
-  if (HALF_IN) dft8_half_in(v, INV); else dft8<float2, float>(v, INV);
+template <bool INV, bool HALF_IN, typename C>
+__device__ __forceinline__ void pass1(C (&v)[8], int a, const C* roots, C* x1, int la) {
+  if (HALF_IN) dft8_half_in(v, INV); else dft8<C, typename RealOf<C>::type>(v, INV);
 #pragma unroll
   for (int c = 1; c < 8; ++c) v[c] = v[c] * root(roots, a * c, INV);
 #pragma unroll
@@ -70,13 +77,12 @@ __device__ __forceinline__ void pass1(float2 (&v)[8], int a, const float2* roots
 }
 
 // pass 2 in thread (c, e): X1[c][e + 8f]  ->  X2[c][g][e]
-template <bool INV>
-__device__ __forceinline__ void pass2(int c, int e, const float2* x1, int la, float2* x2,
-                                      const float2* roots) {
-  float2 u[8];
+template <bool INV, typename C>
+__device__ __forceinline__ void pass2(int c, int e, const C* x1, int la, C* x2, const C* roots) {
+  C u[8];
 #pragma unroll
   for (int f = 0; f < 8; ++f) u[f] = x1[c * la + e + 8 * f];
-  dft8<float2, float>(u, INV);
+  dft8<C, typename RealOf<C>::type>(u, INV);
 #pragma unroll
   for (int g = 1; g < 8; ++g) u[g] = u[g] * root(roots, 8 * e * g, INV);
 #pragma unroll
@@ -84,11 +90,11 @@ __device__ __forceinline__ void pass2(int c, int e, const float2* x1, int la, fl
 }
 
 // pass 3 in thread (c, g): X2[c][g][e]  ->  w[h] = X[c + 8 g + 64 h]
-template <bool INV>
-__device__ __forceinline__ void pass3(int c, int g, const float2* x2, float2 (&w)[8]) {
+template <bool INV, typename C>
+__device__ __forceinline__ void pass3(int c, int g, const C* x2, C (&w)[8]) {
 #pragma unroll
   for (int e = 0; e < 8; ++e) w[e] = x2[c * 72 + 9 * g + e];
-  dft8<float2, float>(w, INV);
+  dft8<C, typename RealOf<C>::type>(w, INV);
 }
 
 // inverse of pass 3 in thread (c, g): w[h] = Y[c + 8g + 64h]  ->  X2[c][g][e]
@@ -461,6 +467,84 @@ __global__ void __launch_bounds__(512, 2) line_tpp_kernel(const LineArgs<float> 
 }
 
 // ---------------------------------------------------------------------------
+// FP64 line stage (the refinement residuals): 4 adjacent columns per CTA, 64
+// threads per column (col = tid & 3, slot t = tid >> 2; a warp's global
+// accesses are 8 rows x 64 contiguous bytes), one exchange buffer per column
+// used as X1 and then X2, twiddles read from the root table.  Bound by FP64
+// arithmetic.
+// ---------------------------------------------------------------------------
+constexpr int kCols64 = 4;
+constexpr int kX64 = 580;
+constexpr size_t kLine64Smem = (size_t)kCols64 * kX64 * sizeof(double2);
+
+template <bool INV, bool HALF>
+__global__ void __launch_bounds__(256, 3) line_tp64_kernel(const LineArgs<double> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, col = tid & 3, t = tid >> 2;
+  double2* x = reinterpret_cast<double2*>(smem_raw) + col * kX64;
+  const int c0 = blockIdx.x * kCols64, o = blockIdx.y, bb = blockIdx.z;
+  pdl_trigger();
+  pdl_wait();
+  if (a.active != nullptr && a.active[bb / a.batch_per_rhs] == 0) return;   // block-uniform
+  const bool col_ok = c0 + col < a.ncol;
+  const double rs = (a.flags & (PRO_RSCALE | EPI_RSCALE))
+                        ? a.rscale[(long long)(bb / a.batch_per_rhs) * a.rscale_stride]
+                        : 1.0;
+  const double2* in = a.in + bb * a.in_bs + o * a.in_os + (long long)(c0 + col);
+  double2 v[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int p = t + kM * b;
+    double2 xv = make_double2(0.0, 0.0);
+    if ((INV || !HALF || b < 4) && col_ok && p < a.lin) {
+      xv = in[(long long)p * a.in_ls];
+      if (!INV) {
+        if (a.flags & PRO_RSCALE) xv = rs * xv;
+        if (a.flags & PRO_CONJ) xv = conjg(xv);
+        if (a.flags & PRO_CHI) xv = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * xv;
+      }
+    }
+    v[b] = xv;
+  }
+  pass1<INV, !INV && HALF>(v, t, a.roots, x, 64);
+  __syncthreads();
+  const int c = t >> 3, g = t & 7;
+  {
+    double2 u[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) u[f] = x[c * 64 + g + 8 * f];
+    dft8<double2, double>(u, INV);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) u[q] = u[q] * root(a.roots, 8 * g * q, INV);
+    __syncthreads();                       // X1 read: X2 overwrites the same buffer
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[c * 72 + 9 * q + g] = u[q];
+  }
+  __syncthreads();
+  pass3<INV>(c, g, x, v);
+  if (!col_ok) return;
+  double2* out = a.out + bb * a.out_bs + o * a.out_os + (long long)(c0 + col);
+#pragma unroll
+  for (int h = 0; h < 8; ++h) {
+    if (INV && HALF && h >= 4) continue;
+    const int p = c + 8 * g + kM * h;
+    if (p >= a.lout) continue;
+    double2 xv = v[h];
+    if (INV) {
+      xv = a.scale * xv;
+      if (a.flags & EPI_CONJ) xv = conjg(xv);
+      if (a.flags & (EPI_SUB | EPI_ADD)) {
+        if (a.flags & EPI_CHI) xv = a.chi[o * a.chi_os + (long long)p * a.chi_ls + (long long)(c0 + col)] * xv;
+        double2 w = a.addend[bb * a.out_bs + o * a.out_os + (long long)(c0 + col) + (long long)p * a.out_ls];
+        if (a.flags & EPI_RSCALE) w = rs * w;
+        xv = (a.flags & EPI_SUB) ? (w - xv) : (w + xv);
+      }
+    }
+    out[(long long)p * a.out_ls] = xv;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused z stage: one CTA of 256 threads per (k1, k2) mirror group, 64 threads
 // per mirror line (thread tid: line l = tid >> 6, slot t = tid & 63).  Each
 // thread carries the three Cartesian components of its line through the
@@ -650,6 +734,24 @@ bool launch_line_tp(LineArgs<float> a, cudaStream_t s) {
   return true;
 }
 
+// FP64 x / y stage of a length-512 line (columns contiguous in memory)
+bool launch_line_tp64(LineArgs<double> a, cudaStream_t s) {
+  if (a.plan.N != tp::kN || a.in_cs != 1 || a.out_cs != 1) return false;
+  if ((a.flags & (PRO_CHI | EPI_CHI)) && a.chi_cs != 1) return false;
+  if (a.nother > 65535 || a.nbatch > 65535) return false;
+  const bool half = a.inverse ? (2 * a.lout == tp::kN) : (2 * a.lin == tp::kN);
+  dim3 grid((a.ncol + tp::kCols64 - 1) / tp::kCols64, a.nother, a.nbatch);
+  a.prof = nullptr;
+  ProfScope ps(a.prof_family, s);
+  if (a.inverse)
+    launch_pdl(half ? tp::line_tp64_kernel<true, true> : tp::line_tp64_kernel<true, false>, grid,
+               dim3(256), tp::kLine64Smem, s, a);
+  else
+    launch_pdl(half ? tp::line_tp64_kernel<false, true> : tp::line_tp64_kernel<false, false>, grid,
+               dim3(256), tp::kLine64Smem, s, a);
+  return true;
+}
+
 // fused z stage over the mirror groups [a.g0, a.g0 + groups) (P3 = 512, n3 <= 256)
 bool fused_tp_supported(const FusedArgs<float>& a, bool stored) {
   return a.P3 == tp::kN && 2 * a.n3 <= tp::kN && (stored || a.octant != nullptr);
@@ -714,7 +816,7 @@ int encode_tensor_map_c64(CUtensorMap* map, const void* base, int rank, const un
   }
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void*>(base), gd,
                         gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? VIE_OK : VIE_ERR_ARG;
 }
 
