@@ -478,6 +478,15 @@ def run_headline(args):
     peak_used = used_bytes() - mem0
     info = op.info()
 
+    # Section V.A's factor-wise setup at the same grid (no stored spectra): time and scratch
+    barrier()
+    t0 = time.perf_counter()
+    op_fw = vie.Operator(n, wl.h, wl.freq_hz, wl.tol_svd, setup="factorwise")
+    barrier()
+    setup_fw_s = time.perf_counter() - t0
+    info_fw = op_fw.info()
+    op_fw.close()
+
     # isolated batched matvecs (the 8 incident fields), both paths
     def matvec_ms(path, reps=3):
         op.matvec(einc, path=path, out=w)
@@ -539,7 +548,11 @@ def run_headline(args):
               "path_total_tucker": mb(dev_t + ws + sws),
               "path_total_uncompressed": mb(dev_s + ws + sws),
               "process_peak_used": mb(peak_used),
-              "setup_s": round(setup_s, 2)}
+              "setup_s": round(setup_s, 2),
+              "setup_scratch": mb(info["setup_scratch_bytes"]),
+              "setup_factorwise_s": round(setup_fw_s, 2),
+              "setup_factorwise_scratch": mb(info_fw["setup_scratch_bytes"]),
+              "setup_factorwise_same_ranks": info_fw["ranks"] == info["ranks"]}
     f = kern_mv.get("fused_tucker")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -81,9 +81,16 @@ enum {
                                     "traditional FFT-JVIE", Table II row 1) in
                                     c64 and c128, for VIE_PATH_UNCOMPRESSED     */
     VIE_SELF_TERM_PV = 2,        /* self term without the -1/3 depolarisation  */
-    VIE_REBUILD_SIMT = 4         /* rebuild the half fibres of eq. (13) with
+    VIE_REBUILD_SIMT = 4,        /* rebuild the half fibres of eq. (13) with
                                     FP32 CUDA-core FMAs instead of the tensor
                                     cores (3xTF32 mma); for comparison          */
+    VIE_SETUP_FACTORWISE = 8     /* Section V.A: compress the Toeplitz defining
+                                    tensor (its parity octant, n1 n2 n3) and
+                                    embed + DFT the factor columns, instead of
+                                    compressing the FFT'd P1 P2 P3 circulant
+                                    tensor; the same ranks and model, without
+                                    forming the P1 P2 P3 spectrum (unless the
+                                    spectra are stored)                          */
 };
 
 /* vie_solve flags */
@@ -144,6 +151,11 @@ typedef struct vie_op_info_t {
     size_t matvec_workspace_bytes; /* matvec scratch T1 + T2 currently held     */
     size_t solver_workspace_bytes; /* Krylov basis, Hessenberg, refinement
                                     vectors currently held (vie_solve)         */
+    size_t setup_scratch_bytes;  /* device scratch vie_tucker_compress held while
+                                    compressing (released before it returned):
+                                    the FP64 P1 P2 P3 spectrum of one component
+                                    (spectrum route, or stored spectra), the
+                                    weighted octant, Gram matrices and vectors  */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */

@@ -27,7 +27,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 VIE_C64, VIE_C128 = 0, 1
 PATHS = {"tucker": 0, "uncompressed": 1, "tucker_cp": 2}
 RANK_RULES = {"tail": 0, "sigma_max": 1}
-VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT = 1, 2, 4
+VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT, VIE_SETUP_FACTORWISE = 1, 2, 4, 8
 REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "tensor_cores"}
 VIE_SOLVE_ADJOINT, VIE_SOLVE_RHS_INCIDENT, VIE_SOLVE_X0 = 1, 2, 4
 COMPONENTS = ("xx", "xy", "xz", "yy", "yz", "zz")
@@ -63,7 +63,7 @@ class OpInfo(ctypes.Structure):
                 ("cp_rel_err", ctypes.c_double * 6), ("cp_sweeps", ctypes.c_int * 6),
                 ("cp_bytes", ctypes.c_size_t), ("device_bytes_tucker", ctypes.c_size_t),
                 ("device_bytes_spectra", ctypes.c_size_t), ("matvec_workspace_bytes", ctypes.c_size_t),
-                ("solver_workspace_bytes", ctypes.c_size_t)]
+                ("solver_workspace_bytes", ctypes.c_size_t), ("setup_scratch_bytes", ctypes.c_size_t)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -181,9 +181,11 @@ class Operator:
     """The compressed J-block operator of a uniform grid (vie_tucker_compress)."""
 
     def __init__(self, n, h, freq_hz, tol, rank_rule="tail", store_uncompressed=False,
-                 self_term="full", rebuild="tensor_cores"):
+                 self_term="full", rebuild="tensor_cores", setup="spectrum"):
         if rebuild not in ("tensor_cores", "simt"):
             raise ValueError("rebuild must be 'tensor_cores' or 'simt'")
+        if setup not in ("spectrum", "factorwise"):
+            raise ValueError("setup must be 'spectrum' or 'factorwise'")
         if isinstance(n, int):
             n = (n, n, n)
         self.n = tuple(int(v) for v in n)
@@ -191,7 +193,8 @@ class Operator:
         self._grid = Grid(self.n[0], self.n[1], self.n[2], self.h, self.freq_hz)
         flags = (VIE_STORE_UNCOMPRESSED if store_uncompressed else 0) | \
                 (VIE_SELF_TERM_PV if self_term == "pv" else 0) | \
-                (VIE_REBUILD_SIMT if rebuild == "simt" else 0)
+                (VIE_REBUILD_SIMT if rebuild == "simt" else 0) | \
+                (VIE_SETUP_FACTORWISE if setup == "factorwise" else 0)
         handle = ctypes.c_void_p()
         _check(lib.vie_tucker_compress(ctypes.byref(self._grid), self.tol, RANK_RULES[rank_rule],
                                        flags, _stream(), ctypes.byref(handle)),
@@ -228,7 +231,8 @@ class Operator:
                 "device_bytes_tucker": inf.device_bytes_tucker,
                 "device_bytes_spectra": inf.device_bytes_spectra,
                 "matvec_workspace_bytes": inf.matvec_workspace_bytes,
-                "solver_workspace_bytes": inf.solver_workspace_bytes}
+                "solver_workspace_bytes": inf.solver_workspace_bytes,
+                "setup_scratch_bytes": inf.setup_scratch_bytes}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""

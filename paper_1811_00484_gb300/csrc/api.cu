@@ -161,7 +161,7 @@ int vie_tucker_compress(const vie_grid* grid, double tol, int rank_rule, int fla
     set_error("unknown rank rule %d", rank_rule);
     return VIE_ERR_ARG;
   }
-  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT)) {
+  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT | VIE_SETUP_FACTORWISE)) {
     set_error("unknown flags 0x%x", flags);
     return VIE_ERR_ARG;
   }
@@ -231,6 +231,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
                                       : 0;
   r.matvec_workspace_bytes = op->ws.bytes;
   r.solver_workspace_bytes = op->solve_ws.bytes;
+  r.setup_scratch_bytes = op->setup_scratch_bytes;
   *info = r;
   return VIE_OK;
 }

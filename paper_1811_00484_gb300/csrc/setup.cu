@@ -129,6 +129,65 @@ __global__ void octant_kernel(const double2* A, double2* Aw, int P1, int P2, int
   }
 }
 
+// Factor-wise route (Section V.A): the weighted octant of the Toeplitz defining
+// tensor itself, T_w[i1, i2, i3] = w(i1) w(i2) w(i3) T_ab(i1 h, i2 h, i3 h) for
+// offsets 0 <= i_q < n_q, w(0) = 1, w(i > 0) = sqrt(2) (offsets +i and -i
+// hold the same entry up to the component's parity sign).
+__global__ void toeplitz_octant_kernel(double2* out, int ca, int cb, int n1, int n2, int n3, double h,
+                                       double k0, double2 self) {
+  const long long total = (long long)n1 * n2 * n3;
+  const double r2 = 1.41421356237309504880;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int o3 = (int)(idx % n3);
+    const int o2 = (int)((idx / n3) % n2);
+    const int o1 = (int)(idx / ((long long)n2 * n3));
+    double2 v = make_double2(0.0, 0.0);
+    if (o1 == 0 && o2 == 0 && o3 == 0) {
+      if (ca == cb) v = self;
+    } else {
+      const double R[3] = {o1 * h, o2 * h, o3 * h};
+      const double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+      double sn, cs;
+      sincos(k0 * r, &sn, &cs);
+      const double inv4pir = 1.0 / (4.0 * kPi * r);
+      const double2 g = make_double2(cs * inv4pir, -sn * inv4pir);
+      const double ir = 1.0 / r;
+      const double2 diag = make_double2(k0 * k0 - ir * ir, -k0 * ir);
+      const double2 dyad = make_double2(-k0 * k0 + 3.0 * ir * ir, 3.0 * k0 * ir);
+      const double rr = (R[ca] * ir) * (R[cb] * ir);
+      double2 f = make_double2(dyad.x * rr, dyad.y * rr);
+      if (ca == cb) f = f + diag;
+      v = (h * h * h) * (g * f);
+    }
+    double w = 1.0;
+    if (o1 != 0) w *= r2;
+    if (o2 != 0) w *= r2;
+    if (o3 != 0) w *= r2;
+    out[idx] = w * v;
+  }
+}
+
+// Rows k = 0 .. P/2 of the embedded, DFT'd factor, normalised to orthonormal
+// columns: out[k][j] = P^-1/2 sum_{|i| < n} U[i][j] exp(-2 pi i k i / P), with
+// U[-i] = s U[i] and the stored rows U[i], i = 0..n-1 (Uh [n][r]):
+//   out[k][j] = P^-1/2 (U[0][j] + sum_{i >= 1} U[i][j] (w^{ki} + s conj(w^{ki}))).
+__global__ void factor_dft_kernel(const double2* Uh, double2* out, const double2* roots, int n, int P,
+                                  int r, int s) {
+  const int total = (P / 2 + 1) * r;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int k = idx / r, j = idx % r;
+    double2 acc = Uh[j];
+    for (int i = 1; i < n; ++i) {
+      const double2 w = roots[(int)(((long long)k * i) % P)];
+      const double2 c = make_double2(w.x + s * w.x, w.y - s * w.y);
+      acc = cmadd(Uh[(long long)i * r + j], c, acc);
+    }
+    const double sc = 1.0 / sqrt((double)P);
+    out[idx] = make_double2(sc * acc.x, sc * acc.y);
+  }
+}
+
 __global__ void to_c64_kernel(const double2* a, float2* b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -364,16 +423,22 @@ static void fft3d_f64(const vie_op* op, double2* a, cudaStream_t s) {
   }
 }
 
-int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s) {
-  int ca, cb;
-  component_axes(c, &ca, &cb);
+// (2/3)(1 + i k0 a) exp(-i k0 a) - 1 (or without the -1/3 part), a = h (3/4pi)^(1/3)
+static double2 self_term_value(const vie_op* op) {
   const double h = op->grid.h, k0 = op->k0;
   const double a = h * std::cbrt(3.0 / (4.0 * kPi));
-  // (2/3)(1 + i k0 a) exp(-i k0 a) - 1, or without the -1/3 part
   const double ca_ = std::cos(k0 * a), sa_ = std::sin(k0 * a);
   double2 self = make_double2((2.0 / 3.0) * (ca_ + k0 * a * sa_) - 1.0,
                               (2.0 / 3.0) * (k0 * a * ca_ - sa_));
   if (op->flags & VIE_SELF_TERM_PV) self.x += 1.0 / 3.0;
+  return self;
+}
+
+int assemble_spectrum(const vie_op* op, int c, double2* out, cudaStream_t s) {
+  int ca, cb;
+  component_axes(c, &ca, &cb);
+  const double h = op->grid.h, k0 = op->k0;
+  const double2 self = self_term_value(op);
   const long long total = (long long)op->P[0] * op->P[1] * op->P[2];
   assemble_kernel<<<grid_for(total), 256, 0, s>>>(out, ca, cb, op->n[0], op->n[1], op->n[2],
                                                    op->P[0], op->P[1], op->P[2], h, k0, self);
@@ -442,40 +507,57 @@ static size_t rank_from_sigma2(const std::vector<double>& s2, double tol, int ru
   return H;
 }
 
-// Compress one component; fills op->comp[c].
+// Compress one component; fills op->comp[c].  Spectrum route: Algorithm 1 on
+// the weighted octant of the FFT'd circulant component.  Factor-wise route
+// (VIE_SETUP_FACTORWISE, Section V.A): Algorithm 1 on the weighted octant of
+// the Toeplitz defining tensor, then the embedding and DFT of each factor
+// column; F_q E_q / sqrt(P_q) is an isometry, so both routes give the same
+// ranks and the same truncated model (core scaled by sqrt(P1 P2 P3)).
 static int compress_component(vie_op* op, int c, double tol, int rule, DeviceBuffers& d,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool factorwise) {
   const int P1 = op->P[0], P2 = op->P[1], P3 = op->P[2];
-  const int H[3] = {op->H[0], op->H[1], op->H[2]};
+  // dimensions of the weighted octant the HOSVD runs on
+  const int H[3] = {factorwise ? op->n[0] : op->H[0], factorwise ? op->n[1] : op->H[1],
+                    factorwise ? op->n[2] : op->H[2]};
   const long long full = (long long)P1 * P2 * P3;
   const long long oct = (long long)H[0] * H[1] * H[2];
   TuckerComp& tc = op->comp[c];
   for (int q = 0; q < 3; ++q) tc.s[q] = component_parity(c, q);
+  const bool need_spectrum = !factorwise || op->spec64 != nullptr;
 
-  VIE_TRY(assemble_spectrum(op, c, d.full, s));
+  if (need_spectrum) {
+    VIE_TRY(assemble_spectrum(op, c, d.full, s));
 
-  // the symmetry every later step relies on
-  VIE_CUDA(cudaMemsetAsync(d.red, 0, 2 * sizeof(unsigned long long), s));
-  parity_check_kernel<<<grid_for(full), 256, 0, s>>>(d.full, P1, P2, P3, tc.s[0], tc.s[1], tc.s[2],
-                                                      d.red);
-  unsigned long long red[2];
-  VIE_CUDA(cudaMemcpyAsync(red, d.red, sizeof(red), cudaMemcpyDeviceToHost, s));
-  VIE_CUDA(cudaStreamSynchronize(s));
-  double dev, mx;
-  std::memcpy(&dev, &red[0], 8);
-  std::memcpy(&mx, &red[1], 8);
-  if (!(dev <= 1e-9 * mx + 1e-300) || !std::isfinite(mx)) {
-    set_error("component %d spectrum breaks its mirror symmetry (%.3e of %.3e)", c, dev, mx);
-    return VIE_ERR_NUMERIC;
+    // the symmetry every later step relies on
+    VIE_CUDA(cudaMemsetAsync(d.red, 0, 2 * sizeof(unsigned long long), s));
+    parity_check_kernel<<<grid_for(full), 256, 0, s>>>(d.full, P1, P2, P3, tc.s[0], tc.s[1], tc.s[2],
+                                                        d.red);
+    unsigned long long red[2];
+    VIE_CUDA(cudaMemcpyAsync(red, d.red, sizeof(red), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    double dev, mx;
+    std::memcpy(&dev, &red[0], 8);
+    std::memcpy(&mx, &red[1], 8);
+    if (!(dev <= 1e-9 * mx + 1e-300) || !std::isfinite(mx)) {
+      set_error("component %d spectrum breaks its mirror symmetry (%.3e of %.3e)", c, dev, mx);
+      return VIE_ERR_NUMERIC;
+    }
+
+    if (op->spec64) {
+      VIE_CUDA(cudaMemcpyAsync(op->spec64 + c * full, d.full, full * sizeof(double2),
+                               cudaMemcpyDeviceToDevice, s));
+      to_c64_kernel<<<grid_for(full), 256, 0, s>>>(d.full, op->spec32 + c * full, full);
+    }
   }
 
-  if (op->spec64) {
-    VIE_CUDA(cudaMemcpyAsync(op->spec64 + c * full, d.full, full * sizeof(double2),
-                             cudaMemcpyDeviceToDevice, s));
-    to_c64_kernel<<<grid_for(full), 256, 0, s>>>(d.full, op->spec32 + c * full, full);
+  if (!factorwise) {
+    octant_kernel<<<grid_for(oct), 256, 0, s>>>(d.full, d.aw, P1, P2, P3, H[0], H[1], H[2]);
+  } else {
+    int ca, cb;
+    component_axes(c, &ca, &cb);
+    toeplitz_octant_kernel<<<grid_for(oct), 256, 0, s>>>(d.aw, ca, cb, H[0], H[1], H[2], op->grid.h,
+                                                          op->k0, self_term_value(op));
   }
-
-  octant_kernel<<<grid_for(oct), 256, 0, s>>>(d.full, d.aw, P1, P2, P3, H[0], H[1], H[2]);
 
   // pass 1: Gram matrices of the three unfoldings and their eigenvectors Y
   for (int q = 0; q < 3; ++q) {
@@ -522,8 +604,11 @@ static int compress_component(vie_op* op, int c, double tol, int rule, DeviceBuf
     double sum = 0.0;
     for (double v : s2) sum += v;
     if (q == 0) norm2 = sum;
-    tc.sigma[q].resize(h);
-    for (int j = 0; j < h; ++j) tc.sigma[q][j] = std::sqrt(s2[j]);
+    // singular values of the spectrum's unfolding (P_q / 2 + 1 of them); the
+    // factor-wise route has those of the Toeplitz tensor's, sqrt(P1 P2 P3) times smaller
+    const double sig_scale = factorwise ? std::sqrt((double)P1 * P2 * P3) : 1.0;
+    tc.sigma[q].assign(op->H[q], 0.0);
+    for (int j = 0; j < h && j < op->H[q]; ++j) tc.sigma[q][j] = sig_scale * std::sqrt(s2[j]);
     // every mode sees the same ||A||_F; use mode 1's sum for all three
     const int r = (int)rank_from_sigma2(s2, tol, rule, norm2);
     tc.r[q] = r;
@@ -544,29 +629,58 @@ static int compress_component(vie_op* op, int c, double tol, int rule, DeviceBuf
   mode_product_kernel<<<grid_for((long long)r1 * H[1] * H[2]), 256, 0, s>>>(
       d.aw, d.tmp, d.vec2[0], r1, 1, 1, H[0], (long long)H[1] * H[2], r1);
   mode_product_kernel<<<grid_for((long long)r1 * r2 * H[2]), 256, 0, s>>>(
-      d.tmp, d.full, d.vec2[1], r2, 1, r1, H[1], H[2], r2);
+      d.tmp, d.aw, d.vec2[1], r2, 1, r1, H[1], H[2], r2);
   mode_product_kernel<<<grid_for((long long)r1 * r2 * r3), 256, 0, s>>>(
-      d.full, d.tmp, d.vec2[2], r3, 1, (long long)r1 * r2, H[2], 1, r3);
+      d.aw, d.tmp, d.vec2[2], r3, 1, (long long)r1 * r2, H[2], 1, r3);
   VIE_CUDA(cudaGetLastError());
   const size_t ncore = (size_t)r1 * r2 * r3;
   VIE_TRY(dalloc(&tc.core64, ncore * sizeof(double2)));
   VIE_TRY(dalloc(&tc.core32, ncore * sizeof(float2)));
+  if (factorwise) {
+    // the spectrum's core: the Toeplitz tensor's times sqrt(P1 P2 P3)
+    const double sc = std::sqrt((double)P1 * P2 * P3);
+    std::vector<double2> hc(ncore);
+    VIE_CUDA(cudaMemcpyAsync(hc.data(), d.tmp, ncore * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    for (auto& v : hc) v = make_double2(sc * v.x, sc * v.y);
+    VIE_CUDA(cudaMemcpy(d.tmp, hc.data(), ncore * sizeof(double2), cudaMemcpyHostToDevice));
+  }
   VIE_CUDA(cudaMemcpyAsync(tc.core64, d.tmp, ncore * sizeof(double2), cudaMemcpyDeviceToDevice, s));
   to_c64_kernel<<<grid_for(ncore), 256, 0, s>>>(tc.core64, tc.core32, (long long)ncore);
 
-  // stored factor rows: U_half = D^-1 Y (rows 0..P/2 of the full factor)
+  // stored factor rows: U_half = D^-1 Y (rows 0..P/2 of the full factor); on the
+  // factor-wise route D^-1 Y are the Toeplitz factor's rows at offsets 0..n-1, which
+  // are embedded and DFT'd into rows 0..P/2 of the spectrum's factor
   for (int q = 0; q < 3; ++q) {
-    const int h = H[q], r = tc.r[q];
+    const int h = op->H[q], r = tc.r[q];
     std::vector<double2> u64((size_t)h * r);
     std::vector<float2> u32((size_t)h * r);
-    for (int i = 0; i < h; ++i) {
-      const double w = (i == 0 || 2 * i == op->P[q]) ? 1.0 : 1.0 / std::sqrt(2.0);
-      for (int j = 0; j < r; ++j) {
-        const double2 v = Ytr[q][(size_t)i * r + j];
-        u64[(size_t)i * r + j] = make_double2(w * v.x, w * v.y);
-        u32[(size_t)i * r + j] = make_float2((float)(w * v.x), (float)(w * v.y));
+    if (!factorwise) {
+      for (int i = 0; i < h; ++i) {
+        const double w = (i == 0 || 2 * i == op->P[q]) ? 1.0 : 1.0 / std::sqrt(2.0);
+        for (int j = 0; j < r; ++j) {
+          const double2 v = Ytr[q][(size_t)i * r + j];
+          u64[(size_t)i * r + j] = make_double2(w * v.x, w * v.y);
+        }
       }
+    } else {
+      const int n = op->n[q];
+      std::vector<double2> ut((size_t)n * r);
+      for (int i = 0; i < n; ++i) {
+        const double w = i == 0 ? 1.0 : 1.0 / std::sqrt(2.0);
+        for (int j = 0; j < r; ++j) {
+          const double2 v = Ytr[q][(size_t)i * r + j];
+          ut[(size_t)i * r + j] = make_double2(w * v.x, w * v.y);
+        }
+      }
+      VIE_CUDA(cudaMemcpy(d.ytr, ut.data(), ut.size() * sizeof(double2), cudaMemcpyHostToDevice));
+      factor_dft_kernel<<<grid_for((long long)h * r), 256, 0, s>>>(d.ytr, d.tmp, op->roots64[q], n,
+                                                                    op->P[q], r, tc.s[q]);
+      VIE_CUDA(cudaGetLastError());
+      VIE_CUDA(cudaMemcpyAsync(u64.data(), d.tmp, u64.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      VIE_CUDA(cudaStreamSynchronize(s));
     }
+    for (size_t i = 0; i < u64.size(); ++i) u32[i] = make_float2((float)u64[i].x, (float)u64[i].y);
     VIE_TRY(dalloc(&tc.U64[q], u64.size() * sizeof(double2)));
     VIE_TRY(dalloc(&tc.U32[q], u32.size() * sizeof(float2)));
     VIE_CUDA(cudaMemcpy(tc.U64[q], u64.data(), u64.size() * sizeof(double2), cudaMemcpyHostToDevice));
@@ -667,7 +781,10 @@ int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, c
   {
     DeviceBuffers d;
     const int hmax = std::max(op->H[0], std::max(op->H[1], op->H[2]));
-    if ((st = dalloc(&d.full, full * sizeof(double2))) != VIE_OK ||
+    const bool factorwise = (flags & VIE_SETUP_FACTORWISE) != 0;
+    // the P1 P2 P3 spectrum is formed only on the spectrum route or to be stored
+    const bool need_full = !factorwise || (flags & VIE_STORE_UNCOMPRESSED);
+    if ((need_full && (st = dalloc(&d.full, full * sizeof(double2))) != VIE_OK) ||
         (st = dalloc(&d.aw, oct * sizeof(double2))) != VIE_OK ||
         (st = dalloc(&d.tmp, std::max(oct, (long long)hmax * hmax) * sizeof(double2))) != VIE_OK ||
         (st = dalloc(&d.ytr, (size_t)hmax * hmax * sizeof(double2))) != VIE_OK ||
@@ -677,13 +794,18 @@ int build_operator(const vie_grid* grid, double tol, int rank_rule, int flags, c
       vie_destroy(op);
       return st;
     }
+    op->setup_scratch_bytes =
+        (need_full ? full * sizeof(double2) : 0) + oct * sizeof(double2) +
+        std::max(oct, (long long)hmax * hmax) * sizeof(double2) + (size_t)hmax * hmax * sizeof(double2);
+    for (int q = 0; q < 3; ++q) op->setup_scratch_bytes += 3 * (size_t)op->H[q] * op->H[q] * sizeof(double2);
     for (int q = 0; q < 3 && st == VIE_OK; ++q) {
       const size_t hh = (size_t)op->H[q] * op->H[q] * sizeof(double2);
       if ((st = dalloc(&d.gram[q], hh)) != VIE_OK || (st = dalloc(&d.vec[q], hh)) != VIE_OK ||
           (st = dalloc(&d.vec2[q], hh)) != VIE_OK)
         break;
     }
-    for (int c = 0; c < 6 && st == VIE_OK; ++c) st = compress_component(op, c, tol, rank_rule, d, s);
+    for (int c = 0; c < 6 && st == VIE_OK; ++c)
+      st = compress_component(op, c, tol, rank_rule, d, s, factorwise);
     if (st == VIE_OK) {
       cudaError_t e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) st = cuda_status(e, "compress");

@@ -233,6 +233,9 @@ struct vie_op {
   // device word that kernels with bounded waits set when a wait gives up
   // (VIE_ERR_TIMEOUT, reported by vie_solve); zero otherwise
   int* dev_err = nullptr;
+  // device scratch the setup held while compressing (spectrum or Toeplitz octant,
+  // Gram matrices, eigenvectors); released before the operator is returned
+  size_t setup_scratch_bytes = 0;
   Workspace ws;
   int ws_batch = 0;
   Tuning tune;

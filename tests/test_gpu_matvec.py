@@ -161,6 +161,47 @@ def test_rebuild_tensor_cores_and_simt(n, tol):
     assert rel(outs["tensor_cores"], outs["simt"]) <= 1e-5
 
 
+@pytest.mark.parametrize("n,tol", [((6, 10, 20), 1e-6), ((16, 16, 16), 1e-8), ((12, 10, 9), 1e-4),
+                                   ((32, 32, 32), 1e-6)])
+def test_factorwise_setup_matches_oracle_and_spectrum_route(n, tol):
+    """Section V.A's route: HOSVD of the Toeplitz defining tensor, then embedding
+    and DFT of the factor columns.  Per component, the device model rebuilt from
+    its exported core and factors equals the oracle's factor-wise model
+    (oracle.factorwise), the ranks equal the spectrum route's (same singular
+    values up to sqrt(P1 P2 P3)), and the two operators' FP64 and FP32
+    matvecs agree; the P1 P2 P3 FP64 spectrum is never formed."""
+    from oracle import factorwise as FW
+    T = K.toeplitz_tensor(*n, HVOX, K0)
+    op_f = vie.Operator(n, HVOX, F, tol, setup="factorwise")
+    op_s = vie.Operator(n, HVOX, F, tol)
+    inf_f, inf_s = op_f.info(), op_s.info()
+    assert inf_f["ranks"] == inf_s["ranks"]
+    P = [2 * v for v in n]
+    assert inf_f["setup_scratch_bytes"] < inf_s["setup_scratch_bytes"] - 0.9 * np.prod(P) * 16
+    for c in range(6):
+        core_o, Uhat_o, sig_o = FW.factorwise_tucker(T[c], tol)
+        A_o = H.tucker_full(core_o, Uhat_o)
+        core, U, sig = op_f.export(c)
+        A_f = H.tucker_full(core, U)
+        assert tuple(core.shape) == tuple(core_o.shape), c
+        assert np.linalg.norm(A_f - A_o) <= 1e-10 * np.linalg.norm(A_o), c
+        core_s, U_s, sig_s = op_s.export(c)
+        assert np.linalg.norm(A_f - H.tucker_full(core_s, U_s)) <= 1e-9 * np.linalg.norm(A_o), c
+        for q in range(3):
+            # the octant has n_q rows: beyond the rank the values are zero (the
+            # oracle's are rounding noise of the full (2 n_q - 1)-row unfolding)
+            k = min(len(sig_o[q]), len(sig[q]), 8)
+            want = np.sqrt(np.prod(P)) * sig_o[q][:k]
+            assert np.allclose(sig[q][:k], want, rtol=1e-9, atol=1e-12 * want[0]), (c, q)
+    J = rand_field(n, B=2, seed=31)
+    y_f = host(op_f.matvec(dev(J, torch.complex128)))
+    y_s = host(op_s.matvec(dev(J, torch.complex128)))
+    assert rel(y_f, y_s) <= 1e-9
+    assert rel(host(op_f.matvec(dev(J))), y_s) <= 1e-5
+    op_f.close()
+    op_s.close()
+
+
 @pytest.mark.parametrize("n", [(3, 4, 5), (6, 10, 20), (16, 16, 16)])
 def test_matvec_uncompressed_paths(n):
     T, Ghat, comp, rebuilt, op = setup_case(n)
