@@ -654,6 +654,7 @@ struct SolverState {
   double2 *H, *cs, *sn, *g, *coef, *partial;
   double *nrm_partial, *nrm, *sig, *beta, *tol_abs, *rnorm, *bnorm, *pb;
   int *active, *iters, *want, *count_it, *count_mv, *again, *ticket;
+  int* mv_active;                   // the matvec's copy of `active` (see arnoldi_step)
   double2 *x, *b64, *r64, *ax64;
   float2* chi32;
   double2* chi64;
@@ -731,7 +732,7 @@ static size_t carve_bytes(int B, int m, long long N, int nchunk, int G, int Gu) 
   for (int i = 0; i < 7; ++i) carve<double>(p, B);    // nrm beta tol_abs rnorm bnorm
   carve<double>(p, (size_t)B * (m + 1));              // sig
   carve<double>(p, (size_t)B * nchunk);               // pb
-  for (int i = 0; i < 7; ++i) carve<int>(p, B);       // active iters want counters again ticket
+  for (int i = 0; i < 8; ++i) carve<int>(p, B);       // active iters want counters again ticket mv_active
   for (int i = 0; i < 4; ++i) carve<double2>(p, (size_t)B * N);   // x b64 r64 ax64
   carve<float2>(p, (size_t)N / 3);                    // chi32
   carve<double2>(p, (size_t)N / 3);                   // chi64
@@ -810,6 +811,7 @@ static int get_state(vie_op* op, int B, int m, SolverState** out) {
   st->count_mv = carve<int>(p, B);
   st->again = carve<int>(p, B);
   st->ticket = carve<int>(p, B);
+  st->mv_active = carve<int>(p, B);
   st->x = carve<double2>(p, (size_t)B * N);
   st->b64 = carve<double2>(p, (size_t)B * N);
   st->r64 = carve<double2>(p, (size_t)B * N);
@@ -848,14 +850,23 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
   const long long N = st->N;
   const float2* vk = st->V + (long long)k * B * N;
   float2* w = st->V + (long long)(k + 1) * B * N;
+  const size_t flag_bytes = (size_t)B * sizeof(int);
+  // The matvec skips right-hand sides by a copy of the active flags taken
+  // before the previous step's Givens step was forked: that step may retire a
+  // right-hand side while the matvec runs, and every thread of every stage
+  // (the producer and consumers of a persistent kernel alike) must take the
+  // same decision for it.  A right-hand side retired meanwhile is still
+  // multiplied; its output is never read.
+  if (k == 0)
+    VIE_CUDA(cudaMemcpyAsync(st->mv_active, st->active, flag_bytes, cudaMemcpyDeviceToDevice, s));
   // w = A (sig_k Vraw_k); the rebuild for the next matvec (the next step's or
   // the cycle tail's) starts beside this step's Gram-Schmidt work
   if (!adjoint)
-    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->active, s,
+    VIE_TRY(matvec_impl<float>(op, vk, w, B, path, 0, EPI_SUB | EPI_CHI, chi, vk, st->mv_active, s,
                                st->sig + k, m + 1));
   else
     VIE_TRY(matvec_impl<float>(op, vk, w, B, path, PRO_CONJ | PRO_CHI, EPI_CONJ | EPI_SUB, chi, vk,
-                               st->active, s, st->sig + k, m + 1));
+                               st->mv_active, s, st->sig + k, m + 1));
   VIE_TRY(join_givens(st, s));
   const unsigned long long vec = (unsigned long long)N * sizeof(float2);
   for (int pass = 0; pass < passes; ++pass) {
@@ -884,7 +895,9 @@ static int arnoldi_step(const vie_op* op, SolverState* st, const float2* chi, in
                  prof_bytes(PF_UPDATE), (k + 3) * vec);
     }
   }
-  // the Givens step beside the next matvec
+  // the Givens step beside the next matvec (which reads the flags as they are now)
+  if (k + 1 < m)
+    VIE_CUDA(cudaMemcpyAsync(st->mv_active, st->active, flag_bytes, cudaMemcpyDeviceToDevice, s));
   VIE_CUDA(cudaEventRecord(st->ev_fork, s));
   VIE_CUDA(cudaStreamWaitEvent(st->aux, st->ev_fork, 0));
   {
