@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-cp", action="store_true", help="skip the Tucker+CP (rank 32) measurement")
     p.add_argument("--mode", default="headline",
                    choices=["headline", "solve64", "matvec", "solve1", "ranks", "tolerance",
-                            "refinement"],
+                            "refinement", "mixed"],
                    help="headline: the 256^3 8-dipole workload (default); solve64: the 64^3 "
                         "plane-wave solve with its extras; matvec: only K timed batched matvecs; "
                         "solve1: K solves only "
@@ -697,6 +697,61 @@ def run_matvec_mode(args):
                       "ms_per_matvec_batch": ms, "matvecs_per_s": args.batch / (ms * 1e-3)}))
 
 
+def run_mixed_mode(args):
+    """The mixed-size batch (48^3, 64^3, 80^3 grids, four ring dipoles each; BASELINE
+    configs[2]'s second part): one multi-grid matvec as one persistent cooperative
+    launch, as one launch per stage, and as separate per-operator matvecs; then the
+    three solves to 1e-6 run concurrently (vie_solve_multi) and one after another."""
+    import numpy as np
+    import torch
+
+    import paper_1811_00484_gb300 as vie
+    import workloads
+
+    wls = workloads.mixed_grids()
+    ops = [vie.Operator(wl.n, wl.h, wl.freq_hz, wl.tol_svd) for wl in wls]
+    chis = [torch.from_numpy(wl.chi.astype(np.complex64)).cuda() for wl in wls]
+    eincs = [op.incident_dipole(wl.dipoles) for op, wl in zip(ops, wls)]
+    Js = [(c[None, None] * e).contiguous() for c, e in zip(chis, eincs)]
+    outs = [torch.empty_like(J) for J in Js]
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    reps = max(args.steps, 10)
+    line = {"mode": "mixed", "grids": [list(wl.n) for wl in wls], "rhs_per_grid": 4,
+            "matvec_ms": {
+                "persistent_one_launch": timed(lambda: vie.matvec_multi(ops, Js, outs, mode="persistent"), reps),
+                "one_launch_per_stage": timed(lambda: vie.matvec_multi(ops, Js, outs, mode="staged"), reps),
+                "separate_operators": timed(lambda: [op.matvec(J, out=o) for op, J, o in zip(ops, Js, outs)],
+                                            reps)}}
+    kw = dict(tol=1e-6, restart=50)
+    vie.solve_multi(ops, chis, eincs, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = [r[1] for r in vie.solve_multi(ops, chis, eincs, **kw)]
+    torch.cuda.synchronize()
+    line["solve_concurrent_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    for op, c, e in zip(ops, chis, eincs):
+        op.solve(c, e, **kw)
+    torch.cuda.synchronize()
+    line["solve_sequential_ms"] = 1e3 * (time.perf_counter() - t0)
+    line["iterations"] = [i["iterations"] for i in infos]
+    print(json.dumps(line))
+    for op in ops:
+        op.close()
+
+
 def smooth7(n):
     """The 7-smooth integer nearest to n (the padded edge 2 n must factor into 2, 3, 5, 7)."""
     def ok(v):
@@ -851,6 +906,8 @@ def main():
         return run_refinement_mode(args)
     if args.mode == "solve64":
         return run_solve64(args)
+    if args.mode == "mixed":
+        return run_mixed_mode(args)
     return run_headline(args)
 
 

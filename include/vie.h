@@ -293,12 +293,23 @@ int vie_matvec_noalloc(const vie_op* op, const void* J, void* Y, int B,
  * Y_p = G_p J_p for `count` operators at once, c64, Tucker path: the batched
  * and mixed-size counterpart of vie_matvec (Section V.B for each operator).
  * Grids of different sizes, each with its own batch B[p], go through one
- * launch per stage (x, y, fused z/rebuild/product, inverse y, inverse x) when every padded edge 2 n_q is 32 R with R in {1..6, 8};
- * otherwise (or for count > 8, in groups of 8) through the per-operator path.
- * ops, J, Y, B: host arrays of `count` entries; J[p], Y[p]: device
- * [B[p]][3][n1][n2][n3] of operator p.  Operators must be distinct (each
- * uses its own scratch).
+ * persistent cooperative launch (vie_matvec_multi_ex with
+ * VIE_MULTI_PERSISTENT): the five stages (x, y, fused z with the rebuild of
+ * each mirror group's half fibres inside its CTA, inverse y, inverse x) run
+ * in turn, every CTA taking the stage's work items of all operators, with a
+ * grid-wide barrier between stages (bounded by one second of the device
+ * timer; a barrier that runs out sets the device error word of ops[0] that
+ * vie_solve reports as VIE_ERR_TIMEOUT).  VIE_MULTI_STAGED launches one
+ * kernel per stage instead.  Both need every padded edge 2 n_q = 32 R with R
+ * in {1..6, 8}; otherwise (or for count > 8, in groups of 8) the problems go
+ * through the per-operator path.  ops, J, B: host arrays of `count` entries;
+ * J[p], Y[p]: device [B[p]][3][n1][n2][n3] of operator p.  Operators must be
+ * distinct (each uses its own scratch).
  */
+enum { VIE_MULTI_PERSISTENT = 0, VIE_MULTI_STAGED = 1 };
+int vie_matvec_multi_ex(const vie_op* const* ops, const void* const* J, void* const* Y,
+                        const int* B, int count, int mode, void* stream);
+/* vie_matvec_multi_ex with VIE_MULTI_PERSISTENT. */
 int vie_matvec_multi(const vie_op* const* ops, const void* const* J,
                      void* const* Y, const int* B, int count, void* stream);
 
@@ -420,7 +431,10 @@ int vie_profile_stop(vie_profile_entry* out, int max_entries, int* count);
  * one thread: with arrive = 1 the barrier's arrival is made first and the
  * call returns VIE_OK; with arrive = 0 nothing arrives, the wait gives up
  * after `seconds` (0 < seconds <= 10) and the call returns VIE_ERR_TIMEOUT.
- * Synchronises `stream`.
+ * arrive = 3 and 2 do the same for the grid barrier of the persistent
+ * multi-grid matvec, in a cooperative launch of two CTAs: with 3 both arrive
+ * (VIE_OK), with 2 the second never does and the first gives up
+ * (VIE_ERR_TIMEOUT).  Synchronises `stream`.
  */
 int vie_selftest_bounded_wait(int arrive, double seconds, void* stream);
 

@@ -38,7 +38,8 @@ EXPORTS = ("vie_tucker_compress", "vie_op_info", "vie_op_export", "vie_green_spe
            "vie_total_field", "vie_solve", "vie_contrast_gradient", "vie_incident_dipole",
            "vie_destroy", "vie_status_string", "vie_last_error", "vie_profile_start",
            "vie_profile_stop", "vie_matvec_noalloc", "vie_matvec_multi", "vie_autotune",
-           "vie_solve_multi", "vie_tucker_cp", "vie_cp_export", "vie_selftest_bounded_wait")
+           "vie_solve_multi", "vie_tucker_cp", "vie_cp_export", "vie_selftest_bounded_wait",
+           "vie_matvec_multi_ex")
 
 
 class VieError(RuntimeError):
@@ -101,6 +102,8 @@ def _load():
         "vie_matvec_noalloc": [vp, vp, vp, ci, vp],
         "vie_matvec_multi": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                              ctypes.POINTER(ci), ci, vp],
+        "vie_matvec_multi_ex": [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                ctypes.POINTER(ci), ci, ci, vp],
         "vie_autotune": [vp, ci, vp],
         "vie_tucker_cp": [vp, ci, cd, ci, ctypes.c_ulonglong, vp],
         "vie_cp_export": [vp, ci, pd, pd, pd, pd, ctypes.POINTER(ci), vp],
@@ -404,8 +407,13 @@ def solve_multi(ops, chis, rhss, incident=True, adjoint=False, tol=1e-6, restart
     return [(w, _solve_info(infs[p], VIE_OK)) for p, w in enumerate(ws)]
 
 
-def matvec_multi(ops, Js, outs=None):
-    """Y_p = G_p J_p for several operators (grids may differ) in one launch per stage."""
+MULTI_MODES = {"persistent": 0, "staged": 1}
+
+
+def matvec_multi(ops, Js, outs=None, mode="persistent"):
+    """Y_p = G_p J_p for several operators (grids may differ): one persistent
+    cooperative launch over all stages (mode "persistent") or one launch per
+    stage ("staged")."""
     torch = _torch()
     count = len(ops)
     if len(Js) != count:
@@ -418,7 +426,8 @@ def matvec_multi(ops, Js, outs=None):
     jp = (ctypes.c_void_p * count)(*[_dev(J, "J", op.n).value for op, J in zip(ops, Js)])
     yp = (ctypes.c_void_p * count)(*[_dev(Y, "out", op.n).value for op, Y in zip(ops, outs)])
     bs = (ctypes.c_int * count)(*[_batch(J, op.n) for op, J in zip(ops, Js)])
-    _check(lib.vie_matvec_multi(hs, jp, yp, bs, count, _stream()), "vie_matvec_multi")
+    _check(lib.vie_matvec_multi_ex(hs, jp, yp, bs, count, MULTI_MODES[mode], _stream()),
+           "vie_matvec_multi_ex")
     return outs
 
 

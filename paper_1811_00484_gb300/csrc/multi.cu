@@ -7,6 +7,7 @@
 // its problem from its block index and runs the same device body as the
 // per-operator kernel, dispatching on that problem's FFT radix R = P / 32.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "stages.cuh"
@@ -85,9 +86,174 @@ __global__ void __launch_bounds__(128) fused_multi_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole matvec of several operators as one persistent cooperative launch:
+// the five stages (x, y, fused z with the rebuild in each CTA, inverse y,
+// inverse x) run one after another, each CTA taking the stage's work items
+// (line tiles or mirror groups of any problem) in steps of the grid, with a
+// grid-wide barrier between stages.  Every CTA of a cooperative launch is
+// resident, so the barrier is met; its wait is still bounded by the device
+// timer, and a CTA that gives up sets the error word and returns.
+// ---------------------------------------------------------------------------
+struct MultiAll {
+  MultiLine line[4];        // x, y, inverse y, inverse x
+  MultiFused fused;
+};
+
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+};
+
+__device__ __forceinline__ unsigned long long global_ns_multi() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// false (in every thread of the CTA) if the other CTAs did not arrive within budget_ns
+__device__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, unsigned long long budget_ns) {
+  __syncthreads();
+  int bad = 0;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns_multi();
+      while (*vgen == g) {
+        if (global_ns_multi() - t0 > budget_ns) {
+          bad = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(bad) == 0;
+}
+
+// RMAX: the largest radix the launch carries (the register budget follows it)
+template <int RMAX>
+__device__ __forceinline__ void multi_line_item(const MultiLine& ml, long long b, float2* smem) {
+  const int p = find_problem(ml.start, ml.count, b);
+  const LineArgs<float>& a = ml.a[p];
+  const long long t = b - ml.start[p];
+  const int ntc = (a.ncol + kLineTile - 1) / kLineTile;
+  const int ct = (int)(t % ntc);
+  const int o = (int)((t / ntc) % a.nother);
+  const int bb = (int)(t / ((long long)ntc * a.nother));
+  switch (ml.R[p]) {
+    case 1: line_warp_tile<1, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 2: line_warp_tile<2, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 3: line_warp_tile<3, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 4: line_warp_tile<4, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 5: if constexpr (RMAX >= 5) line_warp_tile<5, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 6: if constexpr (RMAX >= 6) line_warp_tile<6, true>(a, ct * kLineTile, o, bb, smem); break;
+    case 8: if constexpr (RMAX >= 8) line_warp_tile<8, true>(a, ct * kLineTile, o, bb, smem); break;
+    default: break;
+  }
+}
+
+template <int RMAX>
+__device__ __forceinline__ void multi_fused_item(const MultiFused& mf, long long b, float2* smem) {
+  const int p = find_problem(mf.start, mf.count, b);
+  const int g = (int)(b - mf.start[p]);
+  switch (mf.R[p]) {
+    case 1: fused_warp_group<1, false>(mf.a[p], g, smem); break;
+    case 2: fused_warp_group<2, false>(mf.a[p], g, smem); break;
+    case 3: fused_warp_group<3, false>(mf.a[p], g, smem); break;
+    case 4: fused_warp_group<4, false>(mf.a[p], g, smem); break;
+    case 5: if constexpr (RMAX >= 5) fused_warp_group<5, false>(mf.a[p], g, smem); break;
+    case 6: if constexpr (RMAX >= 6) fused_warp_group<6, false>(mf.a[p], g, smem); break;
+    case 8: if constexpr (RMAX >= 8) fused_warp_group<8, false>(mf.a[p], g, smem); break;
+    default: break;
+  }
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(256, 2) matvec_multi_persistent_kernel(const __grid_constant__ MultiAll m,
+                                                                      GridBarrier* gb, int* err,
+                                                                      unsigned long long budget_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* smem = reinterpret_cast<float2*>(smem_raw);
+  for (int st = 0; st < 5; ++st) {
+    if (st == 2) {
+      const long long total = m.fused.start[m.fused.count];
+      for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+        multi_fused_item<RMAX>(m.fused, b, smem);
+        __syncthreads();                       // shared tables reused by the next item
+      }
+    } else {
+      const MultiLine& ml = m.line[st < 2 ? st : st - 1];
+      const long long total = ml.start[ml.count];
+      for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+        multi_line_item<RMAX>(ml, b, smem);
+        __syncthreads();
+      }
+    }
+    if (st < 4 && !grid_barrier(gb, gridDim.x, budget_ns)) {
+      if (threadIdx.x == 0 && err != nullptr) atomicExch(err, VIE_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
+// self-test of the grid barrier: every CTA but (when skip_last) the last one
+// arrives; status[cta] = 1 if the barrier completed for it, 2 if it gave up
+__global__ void grid_barrier_selftest_kernel(GridBarrier* gb, int skip_last, unsigned long long budget_ns,
+                                             int* status) {
+  if (skip_last && blockIdx.x == gridDim.x - 1) {
+    if (threadIdx.x == 0) status[blockIdx.x] = 0;
+    return;
+  }
+  const bool ok = grid_barrier(gb, gridDim.x, budget_ns);
+  if (threadIdx.x == 0) status[blockIdx.x] = ok ? 1 : 2;
+}
+
 }  // namespace vie
 
 using namespace vie;
+
+// Two co-resident CTAs meet at a grid barrier (all_arrive) or one of them never
+// comes: VIE_OK when the barrier completed, VIE_ERR_TIMEOUT when the waiting
+// CTA gave up after `seconds`.  Its own barrier state, freed afterwards.
+int grid_barrier_selftest(bool all_arrive, double seconds, cudaStream_t s) {
+  GridBarrier* gb = nullptr;
+  int* st = nullptr;
+  int h[2] = {0, 0};
+  cudaError_t e = cudaMalloc(&gb, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = cudaMalloc(&st, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(gb, 0, sizeof(GridBarrier), s);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(64);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, grid_barrier_selftest_kernel, gb, all_arrive ? 0 : 1,
+                           (unsigned long long)(seconds * 1e9), st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, st, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(gb);
+  cudaFree(st);
+  if (e != cudaSuccess) return cuda_status(e, "grid-barrier self-test");
+  if (h[0] == 2) {
+    set_error("the grid barrier gave up after %g s", seconds);
+    return VIE_ERR_TIMEOUT;
+  }
+  return h[0] == 1 && (!all_arrive || h[1] == 1) ? VIE_OK : VIE_ERR_CUDA;
+}
 
 static bool multi_eligible(const vie_op* op) {
   for (int q = 0; q < 3; ++q)
@@ -104,12 +270,42 @@ int multi_init_attributes() {
                              lim);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(matvec_multi_persistent_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(matvec_multi_persistent_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(matvec_multi_persistent_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e == cudaSuccess ? VIE_OK : cuda_status(e, "multi kernel attributes");
 }
 
-// One launch per stage for up to kMaxMulti operators.
+// Grid barrier state of the persistent launch, one per device, allocated once
+// and zeroed (each use leaves the count at zero and advances the generation).
+static int multi_grid_barrier(GridBarrier** out) {
+  static std::mutex mu;
+  static GridBarrier* ptr[64] = {};
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device %d outside the supported range", dev);
+    return VIE_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptr[dev]) {
+    GridBarrier* p = nullptr;
+    VIE_CUDA(cudaMalloc(&p, sizeof(GridBarrier)));
+    VIE_CUDA(cudaMemset(p, 0, sizeof(GridBarrier)));
+    ptr[dev] = p;
+  }
+  *out = ptr[dev];
+  return VIE_OK;
+}
+
+// The matvec of up to kMaxMulti operators: one persistent cooperative launch, or
+// one launch per stage.  VIE_ERR_ARG from the persistent form means it cannot be
+// made co-resident (the caller then uses the staged form).
 static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, float2* const* Y,
-                              const int* B, int count, cudaStream_t s) {
+                              const int* B, int count, bool persistent, cudaStream_t s) {
   std::vector<LineStages<float>> lines(count);
   MultiLine ml[4];
   MultiFused mf;
@@ -140,6 +336,49 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
   }
   for (int st = 0; st < 4; ++st) ml[st].start[count] = lstart[st];
   mf.start[count] = fstart;
+  if (persistent) {
+    MultiAll* all = new MultiAll;
+    for (int st = 0; st < 4; ++st) {
+      all->line[st] = ml[st];
+      for (int p = 0; p < count; ++p) all->line[st].a[p].prof = nullptr;
+    }
+    all->fused = mf;
+    for (int p = 0; p < count; ++p) all->fused.a[p].prof = nullptr;
+    const size_t smem = std::max(smem_line, smem_fused);
+    int rmax = 1;
+    for (int p = 0; p < count; ++p)
+      for (int q = 0; q < 3; ++q) rmax = std::max(rmax, ops[p]->P[q] / 32);
+    using PK = void (*)(MultiAll, GridBarrier*, int*, unsigned long long);
+    const PK kern = rmax <= 4 ? matvec_multi_persistent_kernel<4>
+                              : (rmax <= 6 ? matvec_multi_persistent_kernel<6> : matvec_multi_persistent_kernel<8>);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    long long work = fstart;
+    for (int st = 0; st < 4; ++st) work = std::max(work, lstart[st]);
+    GridBarrier* gb = nullptr;
+    int rc = VIE_OK;
+    if (e != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      rc = VIE_ERR_ARG;   // not co-resident: the caller falls back to the staged launches
+    } else if ((rc = multi_grid_barrier(&gb)) == VIE_OK) {
+      const unsigned grid = (unsigned)std::min<long long>(work, (long long)per_sm * device_sms());
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ProfScope ps(PF_FUSED_TUCKER, s);
+      e = cudaLaunchKernelEx(&cfg, kern, *all, gb, ops[0]->dev_err, (unsigned long long)1000000000ull);
+      if (e != cudaSuccess) rc = cuda_status(e, "persistent multi-grid matvec launch");
+    }
+    delete all;
+    return rc;
+  }
   static const int fam[4] = {PF_LINE_X, PF_LINE_Y, PF_LINE_IY, PF_LINE_IX};
   for (int st = 0; st < 4; ++st) {
     if (st == 2) {
@@ -155,8 +394,13 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
   return VIE_OK;
 }
 
-extern "C" int vie_matvec_multi(const vie_op* const* ops, const void* const* J, void* const* Y,
-                                const int* B, int count, void* stream) {
+extern "C" int vie_matvec_multi_ex(const vie_op* const* ops, const void* const* J, void* const* Y,
+                                   const int* B, int count, int mode, void* stream) {
+  clear_error();
+  if (mode != VIE_MULTI_PERSISTENT && mode != VIE_MULTI_STAGED) {
+    set_error("unknown multi-grid mode %d", mode);
+    return VIE_ERR_ARG;
+  }
   if (!ops || !J || !Y || !B || count < 1) {
     set_error("NULL argument or empty problem list");
     return VIE_ERR_ARG;
@@ -179,10 +423,19 @@ extern "C" int vie_matvec_multi(const vie_op* const* ops, const void* const* J, 
   }
   for (int p0 = 0; p0 < count; p0 += kMaxMulti) {
     const int c = std::min(kMaxMulti, count - p0);
-    VIE_TRY(matvec_multi_chunk(ops + p0, reinterpret_cast<const float2* const*>(J) + p0,
-                               reinterpret_cast<float2* const*>(Y) + p0, B + p0, c, s));
+    const float2* const* Jc = reinterpret_cast<const float2* const*>(J) + p0;
+    float2* const* Yc = reinterpret_cast<float2* const*>(Y) + p0;
+    int rc = VIE_ERR_ARG;
+    if (mode == VIE_MULTI_PERSISTENT) rc = matvec_multi_chunk(ops + p0, Jc, Yc, B + p0, c, true, s);
+    if (rc == VIE_ERR_ARG) rc = matvec_multi_chunk(ops + p0, Jc, Yc, B + p0, c, false, s);
+    VIE_TRY(rc);
   }
   return VIE_OK;
+}
+
+extern "C" int vie_matvec_multi(const vie_op* const* ops, const void* const* J, void* const* Y,
+                                const int* B, int count, void* stream) {
+  return vie_matvec_multi_ex(ops, J, Y, B, count, VIE_MULTI_PERSISTENT, stream);
 }
 
 // Time the FP32 Tucker matvec at batch B with each candidate CTA size of each

@@ -836,13 +836,16 @@ __global__ void bounded_wait_selftest_kernel(int arrive, unsigned long long limi
 }
 }  // namespace vie
 
+int grid_barrier_selftest(bool all_arrive, double seconds, cudaStream_t s);
+
 extern "C" int vie_selftest_bounded_wait(int arrive, double seconds, void* stream) {
   clear_error();
-  if (seconds <= 0.0 || seconds > 10.0) {
-    set_error("wait limit %g s outside (0, 10]", seconds);
+  if (seconds <= 0.0 || seconds > 10.0 || arrive < 0 || arrive > 3) {
+    set_error("wait limit %g s outside (0, 10] or unknown kind %d", seconds, arrive);
     return VIE_ERR_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (arrive >= 2) return grid_barrier_selftest(arrive == 3, seconds, s);
   int* d = nullptr;
   VIE_CUDA(cudaMalloc(&d, sizeof(int)));
   int h = 0;

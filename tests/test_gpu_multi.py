@@ -42,6 +42,10 @@ def test_multi_grid_matvec_matches_single_and_oracle():
     Ys = vie.matvec_multi(ops, Js)
     for op, J, Y in zip(ops, Js, Ys):
         assert rel_t(Y, op.matvec(J)) <= 1e-6
+    # the persistent launch and the launch per stage run the same device bodies
+    Ys2 = vie.matvec_multi(ops, Js, mode="staged")
+    for Y, Y2 in zip(Ys, Ys2):
+        assert torch.equal(Y, Y2)
     k0 = K.wavenumber(298e6)
     n = ns[2]
     Gt = H.rebuild_components(H.compress_components(E.green_spectra(K.toeplitz_tensor(*n, 5e-3, k0), *n), 1e-6))
@@ -82,6 +86,10 @@ def test_multi_falls_back_for_other_edge_lengths():
     Ys = vie.matvec_multi(ops, Js)
     for op, J, Y in zip(ops, Js, Ys):
         assert rel_t(Y, op.matvec(J)) <= 1e-6
+    # the persistent launch and the launch per stage run the same device bodies
+    Ys2 = vie.matvec_multi(ops, Js, mode="staged")
+    for Y, Y2 in zip(Ys, Ys2):
+        assert torch.equal(Y, Y2)
     for op in ops:
         op.close()
 

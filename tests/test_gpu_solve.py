@@ -205,6 +205,11 @@ def test_bounded_device_wait_gives_up_and_reports_timeout():
     assert time.perf_counter() - t0 < 5.0
     assert "gave up" in vie.lib.vie_last_error().decode()
     assert vie.lib.vie_selftest_bounded_wait(0, 0.0, stream) == 1
+    # the grid barrier of the persistent multi-grid matvec: met, and not met
+    assert vie.lib.vie_selftest_bounded_wait(3, 0.05, stream) == 0
+    t0 = time.perf_counter()
+    assert vie.lib.vie_selftest_bounded_wait(2, 0.05, stream) == 6
+    assert time.perf_counter() - t0 < 5.0
     x = torch.ones(8, device="cuda")
     assert float((x * 2).sum()) == 16.0
 
