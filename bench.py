@@ -65,7 +65,7 @@ def parse():
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
-    p.add_argument("--rebuild", default="tensor_cores", choices=["tensor_cores", "simt"],
+    p.add_argument("--rebuild", default="tensor_cores", choices=["tensor_cores", "mma_sync", "simt"],
                    help="matvec / solve1: how the Tucker path rebuilds the Green's fibres")
     p.add_argument("--record-traffic", metavar="NCU_CSV",
                    help="turn an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum per launch "
@@ -698,8 +698,8 @@ def run_matvec_mode(args):
 
 
 def run_mixed_mode(args):
-    """The mixed-size batch (48^3, 64^3, 80^3 grids, four ring dipoles each; BASELINE
-    configs[2]'s second part): one multi-grid matvec as one persistent cooperative
+    """The mixed-size batch (48^3, 64^3, 80^3 grids, four ring dipoles each, beside the
+    96^3 sixteen-dipole batch): one multi-grid matvec as one persistent cooperative
     launch, as one launch per stage, and as separate per-operator matvecs; then the
     three solves to 1e-6 run concurrently (vie_solve_multi) and one after another."""
     import numpy as np

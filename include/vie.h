@@ -84,6 +84,10 @@ enum {
     VIE_REBUILD_SIMT = 4,        /* rebuild the half fibres of eq. (13) with
                                     FP32 CUDA-core FMAs instead of the tensor
                                     cores (3xTF32 mma); for comparison          */
+    VIE_REBUILD_MMA_SYNC = 16,   /* rebuild on the tensor cores through
+                                    warp-level mma.sync (3xTF32) instead of
+                                    tcgen05 with the accumulator in tensor
+                                    memory; for comparison                     */
     VIE_SETUP_FACTORWISE = 8     /* Section V.A: compress the Toeplitz defining
                                     tensor (its parity octant, n1 n2 n3) and
                                     embed + DFT the factor columns, instead of
@@ -133,7 +137,10 @@ typedef struct vie_op_info_t {
     int rebuild_kernel;          /* how each FP32 Tucker matvec rebuilds the
                                     half fibres: 0 inside the fused z-stage
                                     CTAs (no scratch), 1 FP32 FMAs into the
-                                    scratch, 2 tensor cores (3xTF32) into it    */
+                                    scratch, 2 tensor cores through warp-level
+                                    mma.sync (3xTF32) into it, 3 tensor cores
+                                    through tcgen05.mma with TMEM accumulators
+                                    (3xTF32) into it                          */
     int cp_rank;                 /* terms R of the Tucker+CP model (0: none)   */
     double cp_rel_err[6];        /* ||core - CP|| / ||core|| per component;
                                     the factors U^q are orthonormal, so this
@@ -156,6 +163,10 @@ typedef struct vie_op_info_t {
                                     the FP64 P1 P2 P3 spectrum of one component
                                     (spectrum route, or stored spectra), the
                                     weighted octant, Gram matrices and vectors  */
+    int rebuild_tiles[2];        /* rebuild_kernel 3: k3 columns of a CTA's
+                                    range and CTAs per (component, range)
+                                    (vie_autotune's choice, else the default
+                                    of one CTA per SM); 0 otherwise            */
 } vie_op_info_t;
 
 /* vie_solve options (Section VI.C: GMRES, inner 50 / outer 200). */
@@ -316,9 +327,12 @@ int vie_matvec_multi(const vie_op* const* ops, const void* const* J,
 /*
  * Pick the CTA size (64, 128 or 256 threads) of each register-path FFT
  * stage of `op` by timing FP32 Tucker matvecs at batch B on `stream`, and
- * keep the fastest (vie_op_info reports the choice).  Allocates two
- * temporary batches; synchronises `stream`.  Results of later calls do not
- * change, only their speed.
+ * keep the fastest; then, for the tcgen05 rebuild (rebuild_kernel 3), the
+ * tile shape of the rebuild of eq. (13) (k3 columns per CTA and CTAs per
+ * component), timed over every k1 chunk of one matvec.  vie_op_info reports
+ * the choices.  Allocates two temporary batches; synchronises `stream`.
+ * Results of later calls do not change, only their speed.  Do not run it
+ * while another stream uses `op`.
  */
 int vie_autotune(vie_op* op, int B, void* stream);
 

@@ -28,7 +28,8 @@ VIE_C64, VIE_C128 = 0, 1
 PATHS = {"tucker": 0, "uncompressed": 1, "tucker_cp": 2}
 RANK_RULES = {"tail": 0, "sigma_max": 1}
 VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT, VIE_SETUP_FACTORWISE = 1, 2, 4, 8
-REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "tensor_cores"}
+VIE_REBUILD_MMA_SYNC = 16
+REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "mma_sync", 3: "tcgen05"}
 VIE_SOLVE_ADJOINT, VIE_SOLVE_RHS_INCIDENT, VIE_SOLVE_X0 = 1, 2, 4
 COMPONENTS = ("xx", "xy", "xz", "yy", "yz", "zz")
 
@@ -64,7 +65,8 @@ class OpInfo(ctypes.Structure):
                 ("cp_rel_err", ctypes.c_double * 6), ("cp_sweeps", ctypes.c_int * 6),
                 ("cp_bytes", ctypes.c_size_t), ("device_bytes_tucker", ctypes.c_size_t),
                 ("device_bytes_spectra", ctypes.c_size_t), ("matvec_workspace_bytes", ctypes.c_size_t),
-                ("solver_workspace_bytes", ctypes.c_size_t), ("setup_scratch_bytes", ctypes.c_size_t)]
+                ("solver_workspace_bytes", ctypes.c_size_t), ("setup_scratch_bytes", ctypes.c_size_t),
+                ("rebuild_tiles", ctypes.c_int * 2)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -185,8 +187,9 @@ class Operator:
 
     def __init__(self, n, h, freq_hz, tol, rank_rule="tail", store_uncompressed=False,
                  self_term="full", rebuild="tensor_cores", setup="spectrum"):
-        if rebuild not in ("tensor_cores", "simt"):
-            raise ValueError("rebuild must be 'tensor_cores' or 'simt'")
+        # "tensor_cores": tcgen05 where the grid fits it, else warp-level mma.sync
+        if rebuild not in ("tensor_cores", "mma_sync", "simt"):
+            raise ValueError("rebuild must be 'tensor_cores', 'mma_sync' or 'simt'")
         if setup not in ("spectrum", "factorwise"):
             raise ValueError("setup must be 'spectrum' or 'factorwise'")
         if isinstance(n, int):
@@ -197,6 +200,7 @@ class Operator:
         flags = (VIE_STORE_UNCOMPRESSED if store_uncompressed else 0) | \
                 (VIE_SELF_TERM_PV if self_term == "pv" else 0) | \
                 (VIE_REBUILD_SIMT if rebuild == "simt" else 0) | \
+                (VIE_REBUILD_MMA_SYNC if rebuild == "mma_sync" else 0) | \
                 (VIE_SETUP_FACTORWISE if setup == "factorwise" else 0)
         handle = ctypes.c_void_p()
         _check(lib.vie_tucker_compress(ctypes.byref(self._grid), self.tol, RANK_RULES[rank_rule],
@@ -235,7 +239,8 @@ class Operator:
                 "device_bytes_spectra": inf.device_bytes_spectra,
                 "matvec_workspace_bytes": inf.matvec_workspace_bytes,
                 "solver_workspace_bytes": inf.solver_workspace_bytes,
-                "setup_scratch_bytes": inf.setup_scratch_bytes}
+                "setup_scratch_bytes": inf.setup_scratch_bytes,
+                "rebuild_tiles": tuple(inf.rebuild_tiles)}
 
     def export(self, c):
         """(core, [U1, U2, U3], [sigma1, sigma2, sigma3]) of component c as complex128 numpy."""
@@ -274,7 +279,8 @@ class Operator:
         _check(lib.vie_reserve(self._h, int(max_batch)), "vie_reserve")
 
     def autotune(self, batch=1):
-        """Pick the FFT stages' CTA sizes by timing matvecs at `batch` (vie_autotune)."""
+        """Pick the FFT stages' CTA sizes by timing matvecs at `batch`, and the tcgen05
+        rebuild's tile shape (vie_autotune); returns the stages' CTA sizes."""
         _check(lib.vie_autotune(self._h, int(batch), _stream()), "vie_autotune")
         return self.info()["line_threads"]
 

@@ -161,7 +161,8 @@ int vie_tucker_compress(const vie_grid* grid, double tol, int rank_rule, int fla
     set_error("unknown rank rule %d", rank_rule);
     return VIE_ERR_ARG;
   }
-  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT | VIE_SETUP_FACTORWISE)) {
+  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT | VIE_REBUILD_MMA_SYNC |
+                VIE_SETUP_FACTORWISE)) {
     set_error("unknown flags 0x%x", flags);
     return VIE_ERR_ARG;
   }
@@ -198,7 +199,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   r.max_batch = op->ws_batch;
   for (int i = 0; i < 4; ++i) r.line_threads[i] = op->tune.line_threads[i];
   r.tuned_batch = op->tune.tuned_batch;
-  r.rebuild_kernel = op->oct32 == nullptr ? 0 : (octant_uses_tc(op) ? 2 : 1);
+  r.rebuild_kernel = op->oct32 == nullptr ? 0 : op->umma ? 3 : (octant_uses_tc(op) ? 2 : 1);
   r.cp_rank = op->cp.R;
   for (int c = 0; c < 6; ++c) {
     r.cp_rel_err[c] = op->cp.err[c];
@@ -232,6 +233,7 @@ int vie_op_info(const vie_op* op, vie_op_info_t* info) {
   r.matvec_workspace_bytes = op->ws.bytes;
   r.solver_workspace_bytes = op->solve_ws.bytes;
   r.setup_scratch_bytes = op->setup_scratch_bytes;
+  umma_tiles(op, r.rebuild_tiles);
   *info = r;
   return VIE_OK;
 }

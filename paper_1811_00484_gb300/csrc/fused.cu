@@ -921,8 +921,9 @@ static size_t cp_plan(const vie_op* op, int k1a, int nk1, OctCpArgs* t) {
 }
 
 // the rebuild of chunk [k1a, k1a + oct_k1): from the Tucker+CP model (cp), or
-// from the Tucker model on the tensor cores when the operator holds the U3
-// fragments (r3 <= 32 and no VIE_REBUILD_SIMT), else with FMAs
+// from the Tucker model on the tensor cores, through tcgen05 (op->umma) or
+// warp-level mma.sync when the operator holds the U3 fragments (r3 <= 32, no
+// VIE_REBUILD_SIMT), else with FMAs
 int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s, bool cp) {
   const OctArgs o = octant_args(op, k1a);
   const int nk1 = std::min(op->oct_k1, op->H[0] - k1a);
@@ -944,6 +945,7 @@ int launch_octant_args(const vie_op* op, int k1a, cudaStream_t s, bool cp) {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VIE_OK : cuda_status(e, "Tucker+CP rebuild launch");
   }
+  if (op->umma) return launch_octant_umma(op, k1a, nk1, s);
   OctTcArgs t;
   const size_t smem = op->u3frag != nullptr ? tc_plan(op, o, nk1, &t) : 0;
   if (op->u3frag != nullptr && smem <= kTcSmemLimit) {

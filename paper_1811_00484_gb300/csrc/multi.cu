@@ -438,8 +438,47 @@ extern "C" int vie_matvec_multi(const vie_op* const* ops, const void* const* J, 
   return vie_matvec_multi_ex(ops, J, Y, B, count, VIE_MULTI_PERSISTENT, stream);
 }
 
+// Time the per-matvec rebuild (every k1 chunk) of a tcgen05 operator with each
+// tile shape: N ranges per component (the accepted counts) x CTAs per
+// (component, range) (half, one and two times the one-per-SM default); keep
+// the fastest in op->tune.  The tiles change only the speed of the rebuild.
+static int tune_rebuild_tiles(vie_op* op, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  int opts[16];
+  const int nopt = umma_split_options(op, opts, 16);
+  float best = 1e30f;
+  int best_split = 0, best_ctas = 0;
+  for (int i = 0; i < nopt; ++i) {
+    const int d = umma_default_ctas(op, opts[i]);
+    const int ctas[3] = {std::max(1, d / 2), d, 2 * d};
+    for (int ci = 0; ci < 3; ++ci) {
+      op->tune.rb_nsplit = opts[i];
+      op->tune.rb_ctas = ctas[ci];
+      float total = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {              // rep 0 warms up
+        VIE_CUDA(cudaEventRecord(e0, s));
+        for (int k1a = 0; k1a < op->H[0]; k1a += op->oct_k1)
+          VIE_TRY(launch_octant(op, k1a, s, false));
+        VIE_CUDA(cudaEventRecord(e1, s));
+        VIE_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) total += ms;
+      }
+      if (total < best) {
+        best = total;
+        best_split = opts[i];
+        best_ctas = ctas[ci];
+      }
+    }
+  }
+  op->tune.rb_nsplit = best_split;
+  op->tune.rb_ctas = best_ctas;
+  return VIE_OK;
+}
+
 // Time the FP32 Tucker matvec at batch B with each candidate CTA size of each
-// line stage (the other stages at their current choice) and keep the fastest.
+// line stage (the other stages at their current choice) and keep the fastest;
+// then the tile shape of the tcgen05 rebuild.
 extern "C" int vie_autotune(vie_op* op, int B, void* stream) {
   if (!op || B < 1 || B > 4096) {
     set_error("bad operator or batch");
@@ -483,6 +522,9 @@ extern "C" int vie_autotune(vie_op* op, int B, void* stream) {
       }
       op->tune.line_threads[st] = best_t;
     }
+    // the rebuild's scratch is free here: no matvec of this operator is in
+    // flight on another stream while the caller tunes it
+    if (rc == VIE_OK && op->umma && !op->rb_pending) rc = tune_rebuild_tiles(op, s, e0, e1);
     op->tune.tuned_batch = B;
   }
   cudaFree(J);

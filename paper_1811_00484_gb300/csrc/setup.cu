@@ -453,6 +453,7 @@ static int init_tables(vie_op* op) {
   VIE_TRY(fused_init_attributes());
   VIE_TRY(multi_init_attributes());
   VIE_TRY(tp_init_attributes());
+  VIE_TRY(umma_init_attributes());
   for (int q = 0; q < 3; ++q) {
     const int N = op->P[q];
     if (!make_plan(N, &op->plan[q])) {
@@ -737,7 +738,9 @@ static int finish_operator(vie_op* op) {
     VIE_CUDA(cudaStreamCreateWithFlags(&op->rb_stream, cudaStreamNonBlocking));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_fork, cudaEventDisableTiming));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_join, cudaEventDisableTiming));
-    if (tc_rebuild_eligible(op)) {
+    if (!(op->flags & (VIE_REBUILD_SIMT | VIE_REBUILD_MMA_SYNC)) && umma_rebuild_eligible(op)) {
+      op->umma = true;
+    } else if (tc_rebuild_eligible(op)) {
       tc_layout(op->rmax[2], op->H[2], &op->tc_ks, &op->tc_nsplit, &op->tc_ntc);
     }
     if (op->tc_ks > 0 && tc_rebuild_fits(op)) {

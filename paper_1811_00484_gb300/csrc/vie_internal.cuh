@@ -178,6 +178,9 @@ struct Workspace {
 struct Tuning {
   int line_threads[4] = {256, 256, 256, 256};   // x, y, inverse y, inverse x stages
   int tuned_batch = 0;                          // batch the choice was timed at (0 = default)
+  // tcgen05 rebuild tiles: N ranges per component (k3 columns per CTA =
+  // (P3/2) / rb_nsplit) and CTAs per (component, range); 0 = the default plan
+  int rb_nsplit = 0, rb_ctas = 0;
 };
 
 // Tucker+CP model (Algorithm 2, eq. (17)), formed by vie_tucker_cp: factors
@@ -223,6 +226,8 @@ struct vie_op {
   // remainder, in mma fragment order [6][tc_nsplit][tc_ks][tc_ntc][32]
   uint4* u3frag = nullptr;
   int tc_ks = 0, tc_nsplit = 0, tc_ntc = 0;
+  // the rebuild runs on tcgen05 (octant_umma_kernel, umma.cu) instead
+  bool umma = false;
   CpModel cp;
   // stored spectra (optional)
   float2* spec32 = nullptr;  double2* spec64 = nullptr;
@@ -327,6 +332,18 @@ bool tc_rebuild_eligible(const vie_op* op);
 void tc_layout(int r3max, int H3, int* ks, int* nsplit, int* ntc);
 bool tc_rebuild_fits(const vie_op* op);
 int launch_u3_fragments(const vie_op* op, cudaStream_t s);
+// the same rebuild on tcgen05 with TMEM accumulators (umma.cu): whether the
+// operator's sizes fit it, and the launch for nk1 values of k1 from k1a
+bool umma_rebuild_eligible(const vie_op* op);
+int launch_octant_umma(const vie_op* op, int k1a, int nk1, cudaStream_t s);
+// the N-range counts the tcgen05 rebuild accepts for this operator (at most
+// `cap`), and the default CTAs per (component, range) for nsplit ranges
+int umma_split_options(const vie_op* op, int* out, int cap);
+int umma_default_ctas(const vie_op* op, int nsplit);
+// the tiles the tcgen05 rebuild launches with (k3 columns per range, CTAs per
+// (component, range)); zeros when the operator does not use it
+void umma_tiles(const vie_op* op, int out[2]);
+int umma_init_attributes();
 int build_cp_rebuild(vie_op* op, cudaStream_t s);
 void free_cp(vie_op* op);
 

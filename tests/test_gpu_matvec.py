@@ -138,27 +138,34 @@ def test_matvec_register_fft_radices(n):
 @pytest.mark.parametrize("n,tol", [((16, 16, 16), 1e-8), ((16, 18, 32), 1e-6), ((20, 9, 32), 1e-6), ((6, 10, 48), 1e-10),
                                    ((35, 25, 64), 1e-4)])
 def test_rebuild_tensor_cores_and_simt(n, tol):
-    """Both rebuilds of the half fibres of eq. (13) into the scratch, the 3xTF32
-    tensor-core GEMMs and the FP32 FMA kernel, against the oracle's HOSVD.
-    The grids give ragged k2 tiles (H2 = 17, 19, 10, 11, 26: one or three rows
-    left for the FMA path, or a masked mma tile), r3 from a few
-    to past 32 (where the tensor-core kernel hands over to the FMA one)."""
+    """The three rebuilds of the half fibres of eq. (13) into the scratch, the
+    3xTF32 GEMMs on tcgen05 (TMEM accumulators) and on warp-level mma.sync,
+    and the FP32 FMA kernel, against the oracle's HOSVD.  The grids give
+    ragged k2 tiles (H2 = 17, 19, 10, 11, 26: a 128-row tcgen05 tile mostly
+    past H2; one or three rows left for the FMA path of the mma.sync kernel,
+    or a masked mma tile), N ranges of 16 to 64 k3 plus the Nyquist column,
+    and r3 from a few to past 32 (where both tensor-core kernels hand over to
+    the FMA one)."""
     Ghat = E.green_spectra(K.toeplitz_tensor(*n, HVOX, K0), *n)
     rebuilt = H.rebuild_components(H.compress_components(Ghat, tol, "tail"))
     J = rand_field(n, B=3, seed=5)
     ref = M.matvec_fft(rebuilt, J)
     outs = {}
-    for kind in ("tensor_cores", "simt"):
+    for kind, want in (("tensor_cores", "tcgen05"), ("mma_sync", "mma_sync"), ("simt", "simt")):
         op = vie.Operator(n, HVOX, F, tol, rebuild=kind)
         info = op.info()
         r3 = max(r[2] for r in info["ranks"])
-        want = "tensor_cores" if kind == "tensor_cores" and r3 <= 32 else "simt"
-        assert info["rebuild_kernel"] == want
+        assert info["rebuild_kernel"] == (want if r3 <= 32 else "simt")
         assert info["rebuild_scratch_bytes"] > 0
         outs[kind] = host(op.matvec(dev(J)))
         assert rel(outs[kind], ref) <= 1e-5, kind
+        # the adjoint runs the same rebuild on the conjugated model
+        if kind != "simt":
+            y = rand_field(n, B=1, seed=6)
+            assert rel(host(op.matvec_adjoint(dev(y))), AD.adjoint_matvec(rebuilt, y)) <= 1e-5, kind
         op.close()
     assert rel(outs["tensor_cores"], outs["simt"]) <= 1e-5
+    assert rel(outs["mma_sync"], outs["simt"]) <= 1e-5
 
 
 @pytest.mark.parametrize("n,tol", [((6, 10, 20), 1e-6), ((16, 16, 16), 1e-8), ((12, 10, 9), 1e-4),

@@ -94,14 +94,22 @@ def test_multi_falls_back_for_other_edge_lengths():
         op.close()
 
 
-def test_autotune_keeps_results():
-    n = (32, 32, 32)
+@pytest.mark.parametrize("n", [(32, 32, 32), (16, 24, 256)])
+def test_autotune_keeps_results(n):
+    """The autotuner's choices (line-stage CTA sizes; the tcgen05 rebuild's k3
+    columns per CTA and CTAs per component, two range counts to choose from
+    at P3 = 512) change the speed only: the FP32 matvec agrees before and
+    after to FP32 rounding."""
     op = vie.Operator(n, 5e-3, 298e6, 1e-6)
+    assert op.info()["rebuild_kernel"] == "tcgen05"
     J = dev(field(n, 2, 40))
     before = op.matvec(J)
     threads = op.autotune(2)
+    info = op.info()
     assert all(t in (64, 128, 256) for t in threads)
-    assert op.info()["tuned_batch"] == 2
+    assert info["tuned_batch"] == 2
+    nc, ctas = info["rebuild_tiles"]
+    assert (n[2] // nc) * nc == n[2] and nc % 16 == 0 and nc <= 128 and ctas >= 1
     assert rel_t(op.matvec(J), before) <= 1e-6
     op.close()
 
