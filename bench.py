@@ -65,7 +65,7 @@ def parse():
                    help="Gram-Schmidt passes (2 = DGKS-conditional second pass)")
     p.add_argument("--batch", type=int, default=1, help="right-hand sides per matvec (matvec mode)")
     p.add_argument("--path", default="tucker", choices=["tucker", "uncompressed"])
-    p.add_argument("--rebuild", default="tensor_cores", choices=["tensor_cores", "mma_sync", "simt"],
+    p.add_argument("--rebuild", default="tensor_cores", choices=["tensor_cores", "mma_sync", "tcgen05", "simt"],
                    help="matvec / solve1: how the Tucker path rebuilds the Green's fibres")
     p.add_argument("--record-traffic", metavar="NCU_CSV",
                    help="turn an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum per launch "

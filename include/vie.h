@@ -84,10 +84,11 @@ enum {
     VIE_REBUILD_SIMT = 4,        /* rebuild the half fibres of eq. (13) with
                                     FP32 CUDA-core FMAs instead of the tensor
                                     cores (3xTF32 mma); for comparison          */
-    VIE_REBUILD_MMA_SYNC = 16,   /* rebuild on the tensor cores through
-                                    warp-level mma.sync (3xTF32) instead of
-                                    tcgen05 with the accumulator in tensor
-                                    memory; for comparison                     */
+    VIE_REBUILD_TCGEN05 = 16,    /* rebuild on the tensor cores through
+                                    tcgen05.mma with the accumulator in tensor
+                                    memory instead of warp-level mma.sync
+                                    (both 3xTF32); for comparison: slower on
+                                    the rebuild's small K (2 r3)              */
     VIE_SETUP_FACTORWISE = 8     /* Section V.A: compress the Toeplitz defining
                                     tensor (its parity octant, n1 n2 n3) and
                                     embed + DFT the factor columns, instead of

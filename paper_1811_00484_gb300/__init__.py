@@ -28,7 +28,7 @@ VIE_C64, VIE_C128 = 0, 1
 PATHS = {"tucker": 0, "uncompressed": 1, "tucker_cp": 2}
 RANK_RULES = {"tail": 0, "sigma_max": 1}
 VIE_STORE_UNCOMPRESSED, VIE_SELF_TERM_PV, VIE_REBUILD_SIMT, VIE_SETUP_FACTORWISE = 1, 2, 4, 8
-VIE_REBUILD_MMA_SYNC = 16
+VIE_REBUILD_TCGEN05 = 16
 REBUILD_KERNELS = {0: "in_cta", 1: "simt", 2: "mma_sync", 3: "tcgen05"}
 VIE_SOLVE_ADJOINT, VIE_SOLVE_RHS_INCIDENT, VIE_SOLVE_X0 = 1, 2, 4
 COMPONENTS = ("xx", "xy", "xz", "yy", "yz", "zz")
@@ -187,9 +187,10 @@ class Operator:
 
     def __init__(self, n, h, freq_hz, tol, rank_rule="tail", store_uncompressed=False,
                  self_term="full", rebuild="tensor_cores", setup="spectrum"):
-        # "tensor_cores": tcgen05 where the grid fits it, else warp-level mma.sync
-        if rebuild not in ("tensor_cores", "mma_sync", "simt"):
-            raise ValueError("rebuild must be 'tensor_cores', 'mma_sync' or 'simt'")
+        # "tensor_cores" (= "mma_sync"): warp-level mma.sync; "tcgen05": tcgen05.mma
+        # with TMEM accumulators where the grid fits it; "simt": FP32 FMAs
+        if rebuild not in ("tensor_cores", "mma_sync", "tcgen05", "simt"):
+            raise ValueError("rebuild must be 'tensor_cores', 'mma_sync', 'tcgen05' or 'simt'")
         if setup not in ("spectrum", "factorwise"):
             raise ValueError("setup must be 'spectrum' or 'factorwise'")
         if isinstance(n, int):
@@ -200,7 +201,7 @@ class Operator:
         flags = (VIE_STORE_UNCOMPRESSED if store_uncompressed else 0) | \
                 (VIE_SELF_TERM_PV if self_term == "pv" else 0) | \
                 (VIE_REBUILD_SIMT if rebuild == "simt" else 0) | \
-                (VIE_REBUILD_MMA_SYNC if rebuild == "mma_sync" else 0) | \
+                (VIE_REBUILD_TCGEN05 if rebuild == "tcgen05" else 0) | \
                 (VIE_SETUP_FACTORWISE if setup == "factorwise" else 0)
         handle = ctypes.c_void_p()
         _check(lib.vie_tucker_compress(ctypes.byref(self._grid), self.tol, RANK_RULES[rank_rule],

@@ -161,7 +161,7 @@ int vie_tucker_compress(const vie_grid* grid, double tol, int rank_rule, int fla
     set_error("unknown rank rule %d", rank_rule);
     return VIE_ERR_ARG;
   }
-  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT | VIE_REBUILD_MMA_SYNC |
+  if (flags & ~(VIE_STORE_UNCOMPRESSED | VIE_SELF_TERM_PV | VIE_REBUILD_SIMT | VIE_REBUILD_TCGEN05 |
                 VIE_SETUP_FACTORWISE)) {
     set_error("unknown flags 0x%x", flags);
     return VIE_ERR_ARG;

@@ -1,11 +1,17 @@
 // Several operators (grids of different sizes, each with its own batch of
-// right-hand sides) through one launch per matvec stage, and the autotuner
-// that picks the line stages' CTA size.
+// right-hand sides) through one persistent launch or one launch per matvec
+// stage, and the autotuner that picks the line stages' CTA size and the
+// tcgen05 rebuild's tiles.
 //
 // Each multi-grid kernel gets a table of per-problem arguments as a kernel
-// parameter, with the prefix sums of the problems' block counts; a CTA finds
-// its problem from its block index and runs the same device body as the
-// per-operator kernel, dispatching on that problem's FFT radix R = P / 32.
+// parameter, with the prefix sums of the problems' work-item counts; a CTA
+// finds its problem from the item index and runs the device body the
+// per-operator kernels run for that problem's FFT length P = 32 R: for a line
+// item (16 adjacent columns) each of the four warps transforms four columns
+// with the four-step body (R even) or the register lane FFT (R odd), or the
+// CTA runs the shared-memory tile (R = 8); a fused item is one mirror group,
+// four-step (R even, half fibres from the operator's rebuild scratch) or lane
+// FFT.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -23,15 +29,24 @@ constexpr int kMaxMulti = 8;
 struct MultiLine {
   int count;
   int R[kMaxMulti];
+  int vec[kMaxMulti];          // lane FFT rows are 16-byte aligned (two 16-byte accesses per row)
   long long start[kMaxMulti + 1];
   LineArgs<float> a[kMaxMulti];
 };
 struct MultiFused {
   int count;
   int R[kMaxMulti];
+  int fs[kMaxMulti];           // four-step body, half fibres from the rebuild scratch
   long long start[kMaxMulti + 1];
   FusedArgs<float> a[kMaxMulti];
 };
+
+constexpr int kMultiThreads = 128;     // 4 warps x 4 columns = one 16-column line item
+
+// shared memory of a line item of length 32 R (4 warps), and of a fused item
+__host__ __device__ constexpr size_t multi_line_smem(int R) {
+  return R == 8 ? line_warp_smem(8) : (R % 2 == 0 ? line_fs_smem(4 * R, kMultiThreads / 32) : 0);
+}
 
 __device__ __forceinline__ int find_problem(const long long* start, int count, long long b) {
   int p = 0;
@@ -44,46 +59,71 @@ __host__ __device__ constexpr bool multi_radix(int R) {
   return R == 1 || R == 2 || R == 3 || R == 4 || R == 5 || R == 6 || R == 8;
 }
 
-template <bool HALF>
-__global__ void __launch_bounds__(256) line_multi_kernel(const __grid_constant__ MultiLine m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* smem = reinterpret_cast<float2*>(smem_raw);
-  const long long b = blockIdx.x;
-  const int p = find_problem(m.start, m.count, b);
-  const LineArgs<float>& a = m.a[p];
-  const long long t = b - m.start[p];
+// One line item: columns [c0, c0 + 16) of line o of batch entry bb.
+template <int RMAX>
+__device__ __forceinline__ void multi_line_body(const MultiLine& ml, long long b, float2* smem) {
+  const int p = find_problem(ml.start, ml.count, b);
+  const LineArgs<float>& a = ml.a[p];
+  const long long t = b - ml.start[p];
   const int ntc = (a.ncol + kLineTile - 1) / kLineTile;
   const int ct = (int)(t % ntc);
   const int o = (int)((t / ntc) % a.nother);
   const int bb = (int)(t / ((long long)ntc * a.nother));
-  switch (m.R[p]) {
-    case 1: line_warp_tile<1, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 2: line_warp_tile<2, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 3: line_warp_tile<3, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 4: line_warp_tile<4, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 5: line_warp_tile<5, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 6: line_warp_tile<6, HALF>(a, ct * kLineTile, o, bb, smem); break;
-    case 8: line_warp_tile<8, HALF>(a, ct * kLineTile, o, bb, smem); break;
+  const int R = ml.R[p];
+  if (R == 8) {
+    if constexpr (RMAX >= 8) line_warp_tile<8, true>(a, ct * kLineTile, o, bb, smem);
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = ct * kLineTile + warp * kRegCols;
+  if (c0 >= a.ncol) return;                           // warp-uniform; no block barrier here
+  float2* xs = smem + (size_t)warp * kRegCols * fs_col_stride(4 * R);
+  switch (R) {
+    case 1: line_reg_group<1, true>(a, c0, o, bb, ml.vec[p] != 0, lane); break;
+    case 2: line_fs_group<8, true>(a, c0, o, bb, lane, xs); break;
+    case 3: line_reg_group<3, true>(a, c0, o, bb, ml.vec[p] != 0, lane); break;
+    case 4: line_fs_group<16, true>(a, c0, o, bb, lane, xs); break;
+    case 5: if constexpr (RMAX >= 5) line_reg_group<5, true>(a, c0, o, bb, ml.vec[p] != 0, lane); break;
+    case 6: if constexpr (RMAX >= 6) line_fs_group<24, true>(a, c0, o, bb, lane, xs); break;
     default: break;
   }
 }
 
-__global__ void __launch_bounds__(128) fused_multi_kernel(const __grid_constant__ MultiFused m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* smem = reinterpret_cast<float2*>(smem_raw);
-  const long long b = blockIdx.x;
-  const int p = find_problem(m.start, m.count, b);
-  const int g = (int)(b - m.start[p]);
-  switch (m.R[p]) {
-    case 1: fused_warp_group<1, false>(m.a[p], g, smem); break;
-    case 2: fused_warp_group<2, false>(m.a[p], g, smem); break;
-    case 3: fused_warp_group<3, false>(m.a[p], g, smem); break;
-    case 4: fused_warp_group<4, false>(m.a[p], g, smem); break;
-    case 5: fused_warp_group<5, false>(m.a[p], g, smem); break;
-    case 6: fused_warp_group<6, false>(m.a[p], g, smem); break;
-    case 8: fused_warp_group<8, false>(m.a[p], g, smem); break;
+// One fused item: mirror group g of its problem.
+template <int RMAX>
+__device__ __forceinline__ void multi_fused_body(const MultiFused& mf, long long b, float2* smem) {
+  const int p = find_problem(mf.start, mf.count, b);
+  const int g = (int)(b - mf.start[p]);
+  const FusedArgs<float>& a = mf.a[p];
+  if (mf.fs[p]) {
+    switch (mf.R[p]) {
+      case 2: fused_fs_group<8, false>(a, g, smem); break;
+      case 4: fused_fs_group<16, false>(a, g, smem); break;
+      case 6: if constexpr (RMAX >= 6) fused_fs_group<24, false>(a, g, smem); break;
+      default: break;
+    }
+    return;
+  }
+  switch (mf.R[p]) {
+    case 1: fused_warp_group<1, false>(a, g, smem); break;
+    case 2: fused_warp_group<2, false>(a, g, smem); break;
+    case 3: fused_warp_group<3, false>(a, g, smem); break;
+    case 4: fused_warp_group<4, false>(a, g, smem); break;
+    case 5: if constexpr (RMAX >= 5) fused_warp_group<5, false>(a, g, smem); break;
+    case 6: if constexpr (RMAX >= 6) fused_warp_group<6, false>(a, g, smem); break;
+    case 8: if constexpr (RMAX >= 8) fused_warp_group<8, false>(a, g, smem); break;
     default: break;
   }
+}
+
+__global__ void __launch_bounds__(kMultiThreads) line_multi_kernel(const __grid_constant__ MultiLine m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  multi_line_body<8>(m, blockIdx.x, reinterpret_cast<float2*>(smem_raw));
+}
+
+__global__ void __launch_bounds__(kMultiThreads) fused_multi_kernel(const __grid_constant__ MultiFused m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  multi_fused_body<8>(m, blockIdx.x, reinterpret_cast<float2*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -140,44 +180,7 @@ __device__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, unsigned long lo
 
 // RMAX: the largest radix the launch carries (the register budget follows it)
 template <int RMAX>
-__device__ __forceinline__ void multi_line_item(const MultiLine& ml, long long b, float2* smem) {
-  const int p = find_problem(ml.start, ml.count, b);
-  const LineArgs<float>& a = ml.a[p];
-  const long long t = b - ml.start[p];
-  const int ntc = (a.ncol + kLineTile - 1) / kLineTile;
-  const int ct = (int)(t % ntc);
-  const int o = (int)((t / ntc) % a.nother);
-  const int bb = (int)(t / ((long long)ntc * a.nother));
-  switch (ml.R[p]) {
-    case 1: line_warp_tile<1, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 2: line_warp_tile<2, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 3: line_warp_tile<3, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 4: line_warp_tile<4, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 5: if constexpr (RMAX >= 5) line_warp_tile<5, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 6: if constexpr (RMAX >= 6) line_warp_tile<6, true>(a, ct * kLineTile, o, bb, smem); break;
-    case 8: if constexpr (RMAX >= 8) line_warp_tile<8, true>(a, ct * kLineTile, o, bb, smem); break;
-    default: break;
-  }
-}
-
-template <int RMAX>
-__device__ __forceinline__ void multi_fused_item(const MultiFused& mf, long long b, float2* smem) {
-  const int p = find_problem(mf.start, mf.count, b);
-  const int g = (int)(b - mf.start[p]);
-  switch (mf.R[p]) {
-    case 1: fused_warp_group<1, false>(mf.a[p], g, smem); break;
-    case 2: fused_warp_group<2, false>(mf.a[p], g, smem); break;
-    case 3: fused_warp_group<3, false>(mf.a[p], g, smem); break;
-    case 4: fused_warp_group<4, false>(mf.a[p], g, smem); break;
-    case 5: if constexpr (RMAX >= 5) fused_warp_group<5, false>(mf.a[p], g, smem); break;
-    case 6: if constexpr (RMAX >= 6) fused_warp_group<6, false>(mf.a[p], g, smem); break;
-    case 8: if constexpr (RMAX >= 8) fused_warp_group<8, false>(mf.a[p], g, smem); break;
-    default: break;
-  }
-}
-
-template <int RMAX>
-__global__ void __launch_bounds__(256, 2) matvec_multi_persistent_kernel(const __grid_constant__ MultiAll m,
+__global__ void __launch_bounds__(kMultiThreads, 4) matvec_multi_persistent_kernel(const __grid_constant__ MultiAll m,
                                                                       GridBarrier* gb, int* err,
                                                                       unsigned long long budget_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -186,14 +189,14 @@ __global__ void __launch_bounds__(256, 2) matvec_multi_persistent_kernel(const _
     if (st == 2) {
       const long long total = m.fused.start[m.fused.count];
       for (long long b = blockIdx.x; b < total; b += gridDim.x) {
-        multi_fused_item<RMAX>(m.fused, b, smem);
+        multi_fused_body<RMAX>(m.fused, b, smem);
         __syncthreads();                       // shared tables reused by the next item
       }
     } else {
       const MultiLine& ml = m.line[st < 2 ? st : st - 1];
       const long long total = ml.start[ml.count];
       for (long long b = blockIdx.x; b < total; b += gridDim.x) {
-        multi_line_item<RMAX>(ml, b, smem);
+        multi_line_body<RMAX>(ml, b, smem);
         __syncthreads();
       }
     }
@@ -263,11 +266,7 @@ static bool multi_eligible(const vie_op* op) {
 
 int multi_init_attributes() {
   const int lim = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(line_multi_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(line_multi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             lim);
+  cudaError_t e = cudaFuncSetAttribute(line_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess)
@@ -307,6 +306,7 @@ static int multi_grid_barrier(GridBarrier** out) {
 static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, float2* const* Y,
                               const int* B, int count, bool persistent, cudaStream_t s) {
   std::vector<LineStages<float>> lines(count);
+  std::vector<char> prebuilt(count, 0);
   MultiLine ml[4];
   MultiFused mf;
   size_t smem_line = 0, smem_fused = 0;
@@ -323,16 +323,41 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
       a.prof = prof_bytes(a.prof_family);
       ml[st].a[p] = a;
       ml[st].R[p] = a.plan.N / 32;
+      // 16-byte row accesses of the lane FFT: every row of every group starts
+      // on a 16-byte boundary
+      ml[st].vec[p] = a.in_bs % 2 == 0 && a.in_os % 2 == 0 && a.in_ls % 2 == 0 && a.out_bs % 2 == 0 &&
+                      a.out_os % 2 == 0 && a.out_ls % 2 == 0 && ((uintptr_t)a.in & 15u) == 0 &&
+                      ((uintptr_t)a.out & 15u) == 0;
       ml[st].start[p] = lstart[st];
       lstart[st] += (long long)((a.ncol + kLineTile - 1) / kLineTile) * a.nother * a.nbatch;
-      smem_line = std::max(smem_line, line_warp_smem(a.plan.N / 32));
+      smem_line = std::max(smem_line, multi_line_smem(a.plan.N / 32));
     }
     float2* T2 = lines[p].s[1].out;
     mf.a[p] = make_fused_args<float>(op, T2, B[p], false, nullptr);
+    // An operator whose rebuild scratch holds every k1 has its half fibres
+    // rebuilt once by its own rebuild kernel (on its side stream, after the
+    // work already on s) and shared by all its right-hand sides; the fused
+    // items then copy them instead of rebuilding them in each CTA.
+    if (op->oct32 != nullptr && op->rb_stream != nullptr && op->oct_k1 >= op->H[0]) {
+      if (!(op->rb_pending && !op->rb_cp)) {
+        VIE_CUDA(cudaEventRecord(op->rb_fork, s));
+        VIE_CUDA(cudaStreamWaitEvent(op->rb_stream, op->rb_fork, 0));
+        VIE_TRY(launch_octant(op, 0, op->rb_stream, false));
+        VIE_CUDA(cudaEventRecord(op->rb_join, op->rb_stream));
+      }
+      const_cast<vie_op*>(op)->rb_pending = false;
+      prebuilt[p] = true;
+      mf.a[p].octant = op->oct32;
+      mf.a[p].oct_k1a = 0;
+      mf.a[p].oct_chunk = op->oct_k1;
+    }
     mf.R[p] = op->P[2] / 32;
+    mf.fs[p] = prebuilt[p] && mf.R[p] % 2 == 0 && mf.R[p] <= 6;
     mf.start[p] = fstart;
     fstart += (long long)op->H[0] * op->H[1];
-    smem_fused = std::max(smem_fused, fused_warp_smem(op->P[2] / 32, op->H[2], op->rmax[1], op->rmax[2]));
+    smem_fused = std::max(smem_fused, mf.fs[p] ? fused_fs_smem(4 * mf.R[p], op->H[2])
+                                               : fused_warp_smem(op->P[2] / 32, op->H[2], op->rmax[1],
+                                                                 op->rmax[2]));
   }
   for (int st = 0; st < 4; ++st) ml[st].start[count] = lstart[st];
   mf.start[count] = fstart;
@@ -352,7 +377,7 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
     const PK kern = rmax <= 4 ? matvec_multi_persistent_kernel<4>
                               : (rmax <= 6 ? matvec_multi_persistent_kernel<6> : matvec_multi_persistent_kernel<8>);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMultiThreads, smem);
     long long work = fstart;
     for (int st = 0; st < 4; ++st) work = std::max(work, lstart[st]);
     GridBarrier* gb = nullptr;
@@ -362,9 +387,12 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
       rc = VIE_ERR_ARG;   // not co-resident: the caller falls back to the staged launches
     } else if ((rc = multi_grid_barrier(&gb)) == VIE_OK) {
       const unsigned grid = (unsigned)std::min<long long>(work, (long long)per_sm * device_sms());
+      for (int p = 0; p < count && rc == VIE_OK; ++p)
+        if (prebuilt[p] && cudaStreamWaitEvent(s, ops[p]->rb_join, 0) != cudaSuccess)
+          rc = cuda_status(cudaGetLastError(), "rebuild join");
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(grid);
-      cfg.blockDim = dim3(256);
+      cfg.blockDim = dim3(kMultiThreads);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
@@ -372,9 +400,11 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
       attr[0].val.cooperative = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      ProfScope ps(PF_FUSED_TUCKER, s);
-      e = cudaLaunchKernelEx(&cfg, kern, *all, gb, ops[0]->dev_err, (unsigned long long)1000000000ull);
-      if (e != cudaSuccess) rc = cuda_status(e, "persistent multi-grid matvec launch");
+      if (rc == VIE_OK) {
+        ProfScope ps(PF_FUSED_TUCKER, s);
+        e = cudaLaunchKernelEx(&cfg, kern, *all, gb, ops[0]->dev_err, (unsigned long long)1000000000ull);
+        if (e != cudaSuccess) rc = cuda_status(e, "persistent multi-grid matvec launch");
+      }
     }
     delete all;
     return rc;
@@ -382,12 +412,14 @@ static int matvec_multi_chunk(const vie_op* const* ops, const float2* const* J, 
   static const int fam[4] = {PF_LINE_X, PF_LINE_Y, PF_LINE_IY, PF_LINE_IX};
   for (int st = 0; st < 4; ++st) {
     if (st == 2) {
+      for (int p = 0; p < count; ++p)
+        if (prebuilt[p]) VIE_CUDA(cudaStreamWaitEvent(s, ops[p]->rb_join, 0));
       ProfScope ps(PF_FUSED_TUCKER, s);
-      fused_multi_kernel<<<(unsigned)fstart, 128, smem_fused, s>>>(mf);
+      fused_multi_kernel<<<(unsigned)fstart, kMultiThreads, smem_fused, s>>>(mf);
     }
     ProfScope ps(fam[st], s);
     // every stage of every operator is a half-length transform (zero pad or crop)
-    line_multi_kernel<true><<<(unsigned)lstart[st], 256, smem_line, s>>>(ml[st]);
+    line_multi_kernel<<<(unsigned)lstart[st], kMultiThreads, smem_line, s>>>(ml[st]);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "multi-grid matvec launch");

@@ -738,7 +738,7 @@ static int finish_operator(vie_op* op) {
     VIE_CUDA(cudaStreamCreateWithFlags(&op->rb_stream, cudaStreamNonBlocking));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_fork, cudaEventDisableTiming));
     VIE_CUDA(cudaEventCreateWithFlags(&op->rb_join, cudaEventDisableTiming));
-    if (!(op->flags & (VIE_REBUILD_SIMT | VIE_REBUILD_MMA_SYNC)) && umma_rebuild_eligible(op)) {
+    if ((op->flags & VIE_REBUILD_TCGEN05) && !(op->flags & VIE_REBUILD_SIMT) && umma_rebuild_eligible(op)) {
       op->umma = true;
     } else if (tc_rebuild_eligible(op)) {
       tc_layout(op->rmax[2], op->H[2], &op->tc_ks, &op->tc_nsplit, &op->tc_ntc);

@@ -597,7 +597,8 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
   constexpr int XS = fs_col_stride(V);
   constexpr int SS = fused_fs_spec_stride(V);
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, comp = tid >> 5;  // three warps
+  const int lane = tid & 31, comp = tid >> 5;  // three warps (a fourth, if any, only helps copy)
+  const bool act = comp < 3;
   const int j = lane >> 2, ln = lane & 3;
   const int n3 = a.n3, H3 = a.H3;
   const int k1 = g / a.H2, k2 = g % a.H2;
@@ -610,7 +611,7 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
   const int GS = ghalf_slot(H3 - 1) + 1;
   C* ghalf = smem;                              // [6][GS]
   C* spec = ghalf + 6 * GS;                     // [3][4][SS]
-  C* xw = spec + 3 * 4 * SS + comp * kRegCols * XS;   // this warp's exchange buffer
+  C* xw = spec + 3 * 4 * SS + (act ? comp : 0) * kRegCols * XS;   // this warp's exchange buffer
   C* xc = xw + ln * XS;
   pdl_trigger();
   pdl_wait();
@@ -636,9 +637,10 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
   __syncthreads();
   for (int b = 0; b < a.B; ++b) {
     if (a.active != nullptr && a.active[b] == 0) continue;   // block-uniform
-    C* line = a.data + (long long)(b * 3 + comp) * a.comp_stride + line_off;
-    // forward pass 1: x[j + 8 m], m < V/2 (the rest is zero padding)
+    C* line = a.data + (long long)(b * 3 + (act ? comp : 0)) * a.comp_stride + line_off;
     C v[V];
+    if (act) {
+    // forward pass 1: x[j + 8 m], m < V/2 (the rest is zero padding)
 #pragma unroll
     for (int m = 0; m < V; ++m) {
       const int p = j + 8 * m;
@@ -662,7 +664,9 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
 #pragma unroll
       for (int k = 0; k < 8; ++k) sp[q + V * k] = u[k];
     }
+    }
     __syncthreads();
+    if (act) {
     // product at f = j + 8 m, straight into the inverse pass 1 registers
     const C* s0 = spec + (0 * 4 + ln) * SS;
     const C* s1 = spec + (1 * 4 + ln) * SS;
@@ -712,6 +716,7 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
         const int n = q + V * k;
         if (valid && n < n3) line[n] = u[k];
       }
+    }
     }
     __syncthreads();                           // spec and xw reused by the next right-hand side
   }

@@ -53,7 +53,7 @@ struct OctUmmaArgs {
   const CompMeta<float>* meta;
   float2* out;       // [nk1][H2][6][H3]
   int H2, H3;
-  int r3max;         // row stride of the slab cores [H1][r2max][r3max]
+  int r2max, r3max;  // slab cores [H1][r2max][r3max]
   int r23;           // r2max * r3max
   int k1a, nk1;
   int mt;            // 128-row tiles of k2
@@ -66,10 +66,16 @@ struct OctUmmaArgs {
 
 __host__ __device__ constexpr int um_k(int r3) { return (2 * r3 + 7) & ~7; }
 
-__host__ __device__ constexpr size_t um_smem(int N, int kp) {
+// U2 rows staged with an odd float2 stride: the A-build's row-per-thread
+// reads are then free of bank conflicts
+__host__ __device__ constexpr int um_r2p(int r2max) { return r2max | 1; }
+
+__host__ __device__ constexpr size_t um_smem(int N, int kp, int H2, int r2max, int r3max) {
   return (size_t)2 * N * kp * sizeof(float) +                  // B hi, lo
          (size_t)4 * kUmRows * kp * sizeof(float) +            // A [2 buffers][hi, lo]
          (size_t)(kUmThreads / 32) * kUmStage * sizeof(float) + // epilogue staging
+         ((size_t)H2 * um_r2p(r2max) +                          // U2 of the component
+          (size_t)r2max * r3max + r3max) * sizeof(float2) +     // S[k1], U3[P3/2, :]
          1024;                                                  // alignment slack
 }
 
@@ -145,6 +151,10 @@ __global__ void __launch_bounds__(kUmThreads, 1) octant_umma_kernel(const OctUmm
   float* Blo = Bhi + (size_t)N * kp;
   float* Abuf = Blo + (size_t)N * kp;                     // [buffer][hi, lo][128 kp]
   float* stage = Abuf + (size_t)4 * kUmRows * kp + warp * kUmStage;
+  const int r2p = um_r2p(a.r2max);
+  float2* U2s = reinterpret_cast<float2*>(Abuf + (size_t)4 * kUmRows * kp + (kUmThreads / 32) * kUmStage);
+  float2* Ss = U2s + (size_t)H2 * r2p;                    // [r2][r3max] of the unit's k1
+  float2* U3n = Ss + (size_t)a.r2max * a.r3max;           // U3[H3 - 1, q]
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -157,18 +167,47 @@ __global__ void __launch_bounds__(kUmThreads, 1) octant_umma_kernel(const OctUmm
     mbar_init(&mbar[1], 1);
     mbar_fence_init();
   }
-  // B (hi, lo) of this CTA's columns; A buffers zeroed (their K padding stays 0)
-  for (int i = tid; i < N * K; i += kUmThreads) {
-    const int j = i / K, k = i - j * K;
-    const int q = k >> 1, k3 = sp * a.NC + (j >> 1);
-    float2 u = make_float2(0.f, 0.f);
-    if (q < r3) u = m.U3t[(long long)q * H3 + k3];
-    const float v = (j & 1) ? ((k & 1) ? u.x : u.y) : ((k & 1) ? -u.y : u.x);
-    const uint32_t hi = um_tf32(v);
-    const int o = um_off(j, k, K);
-    Bhi[o] = __uint_as_float(hi);
-    Blo[o] = __uint_as_float(um_tf32(v - __uint_as_float(hi)));
+  // B (hi, lo) of this CTA's columns, eight loads in flight per thread; the U2
+  // rows and U3[P3/2, :] of the component; A buffers zeroed (K padding stays 0)
+  for (int i0 = tid; i0 < N * K; i0 += 8 * kUmThreads) {
+    float2 u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = i0 + e * kUmThreads;
+      const int j = i / K, k = i - j * K, q = k >> 1;
+      u[e] = (i < N * K && q < r3) ? __ldg(m.U3t + (long long)q * H3 + sp * a.NC + (j >> 1))
+                                   : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = i0 + e * kUmThreads;
+      if (i < N * K) {
+        const int j = i / K, k = i - j * K;
+        const float v = (j & 1) ? ((k & 1) ? u[e].x : u[e].y) : ((k & 1) ? -u[e].y : u[e].x);
+        const uint32_t hi = um_tf32(v);
+        const int o = um_off(j, k, K);
+        Bhi[o] = __uint_as_float(hi);
+        Blo[o] = __uint_as_float(um_tf32(v - __uint_as_float(hi)));
+      }
+    }
   }
+  for (int i0 = tid; i0 < H2 * r2; i0 += 8 * kUmThreads) {
+    float2 u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = i0 + e * kUmThreads;
+      u[e] = i < H2 * r2 ? __ldg(m.U2 + i) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = i0 + e * kUmThreads;
+      if (i < H2 * r2) {
+        const int k2 = i / r2;
+        U2s[k2 * r2p + (i - k2 * r2)] = u[e];
+      }
+    }
+  }
+  if (tid < r3) U3n[tid] = __ldg(m.U3t + (long long)tid * H3 + (H3 - 1));
   for (int i = tid; i < 4 * kUmRows * kp; i += kUmThreads) Abuf[i] = 0.f;
   fence_proxy_async_smem();
   um_fence_before();
@@ -183,7 +222,6 @@ __global__ void __launch_bounds__(kUmThreads, 1) octant_umma_kernel(const OctUmm
   const int row = tid & (kUmRows - 1), qh = tid >> 7;
   const int qa = qh ? (r3 + 1) / 2 : 0, qb = qh ? r3 : (r3 + 1) / 2;
   const bool nyq = sp == a.nsplit - 1;
-  const float2* U3n = m.U3t + (H3 - 1);                   // U3[H3 - 1, q] at U3n[q H3]
   int fail_it = -1, fail_u = -1;
 
   for (int u = u0, it = 0; u <= u1; ++u, ++it) {
@@ -192,13 +230,20 @@ __global__ void __launch_bounds__(kUmThreads, 1) octant_umma_kernel(const OctUmm
     float* Alo = Ahi + (size_t)kUmRows * kp;
     const int k1l = u / a.mt, k2 = (u - k1l * a.mt) * kUmRows + row;
     if (u < u1) {
+      // the slab core S[k1] of the unit (the previous unit's readers passed
+      // the barrier after its A-build)
+      {
+        const float2* S = m.slab + (long long)(a.k1a + k1l) * a.r23;
+        for (int i = tid; i < r2 * a.r3max; i += kUmThreads) Ss[i] = __ldg(S + i);
+      }
+      __syncthreads();
       // W[k2, q] = sum_b U2[k2, b] S[k1][b, q] for this thread's half of q
       float2 w[kUmMaxR3 / 2];
 #pragma unroll
       for (int j = 0; j < kUmMaxR3 / 2; ++j) w[j] = make_float2(0.f, 0.f);
       if (k2 < H2) {
-        const float2* S = m.slab + (long long)(a.k1a + k1l) * a.r23 + qa;
-        const float2* u2 = m.U2 + (long long)k2 * r2;
+        const float2* S = Ss + qa;
+        const float2* u2 = U2s + k2 * r2p;
         for (int bb = 0; bb < r2; ++bb) {
           const float2 uv = u2[bb];
           const float2* Sb = S + bb * a.r3max;
@@ -243,7 +288,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) octant_umma_kernel(const OctUmm
           const int o = um_off(row, 2 * q, K);
           const float2 h = *reinterpret_cast<const float2*>(Ahi + o);
           const float2 l = *reinterpret_cast<const float2*>(Alo + o);
-          acc = cmadd(make_float2(h.x + l.x, h.y + l.y), U3n[(long long)q * H3], acc);
+          acc = cmadd(make_float2(h.x + l.x, h.y + l.y), U3n[q], acc);
         }
         a.out[(((long long)k1l * H2 + k2) * 6 + c) * H3 + (H3 - 1)] = acc;
       }
@@ -308,7 +353,8 @@ static bool umma_split_ok(const vie_op* op, int nsplit) {
   const int H3m = op->H[2] - 1;
   if (nsplit < 1 || H3m % nsplit) return false;
   const int NC = H3m / nsplit;
-  return NC % 16 == 0 && NC <= 128 && um_smem(2 * NC, um_k(op->rmax[2])) <= kUmSmemLimit;
+  return NC % 16 == 0 && NC <= 128 &&
+         um_smem(2 * NC, um_k(op->rmax[2]), op->H[1], op->rmax[1], op->rmax[2]) <= kUmSmemLimit;
 }
 
 int umma_split_options(const vie_op* op, int* out, int cap) {
@@ -338,6 +384,7 @@ static bool umma_plan(const vie_op* op, int k1a, int nk1, vie::OctUmmaArgs* a, s
   a->out = op->oct32;
   a->H2 = op->H[1];
   a->H3 = op->H[2];
+  a->r2max = op->rmax[1];
   a->r3max = op->rmax[2];
   a->r23 = op->rmax[1] * op->rmax[2];
   a->k1a = k1a;
@@ -354,7 +401,7 @@ static bool umma_plan(const vie_op* op, int k1a, int nk1, vie::OctUmmaArgs* a, s
   const int ctas = op->tune.rb_ctas > 0 ? op->tune.rb_ctas : umma_default_ctas(op, nsplit);
   const int gy = std::max(1, std::min(units, ctas));
   a->per = (units + gy - 1) / gy;
-  *smem = um_smem(2 * a->NC, kp);
+  *smem = um_smem(2 * a->NC, kp, op->H[1], op->rmax[1], op->rmax[2]);
   return true;
 }
 

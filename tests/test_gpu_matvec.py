@@ -151,7 +151,7 @@ def test_rebuild_tensor_cores_and_simt(n, tol):
     J = rand_field(n, B=3, seed=5)
     ref = M.matvec_fft(rebuilt, J)
     outs = {}
-    for kind, want in (("tensor_cores", "tcgen05"), ("mma_sync", "mma_sync"), ("simt", "simt")):
+    for kind, want in (("tensor_cores", "mma_sync"), ("tcgen05", "tcgen05"), ("simt", "simt")):
         op = vie.Operator(n, HVOX, F, tol, rebuild=kind)
         info = op.info()
         r3 = max(r[2] for r in info["ranks"])
@@ -165,7 +165,7 @@ def test_rebuild_tensor_cores_and_simt(n, tol):
             assert rel(host(op.matvec_adjoint(dev(y))), AD.adjoint_matvec(rebuilt, y)) <= 1e-5, kind
         op.close()
     assert rel(outs["tensor_cores"], outs["simt"]) <= 1e-5
-    assert rel(outs["mma_sync"], outs["simt"]) <= 1e-5
+    assert rel(outs["tcgen05"], outs["simt"]) <= 1e-5
 
 
 @pytest.mark.parametrize("n,tol", [((6, 10, 20), 1e-6), ((16, 16, 16), 1e-8), ((12, 10, 9), 1e-4),

@@ -100,7 +100,7 @@ def test_autotune_keeps_results(n):
     columns per CTA and CTAs per component, two range counts to choose from
     at P3 = 512) change the speed only: the FP32 matvec agrees before and
     after to FP32 rounding."""
-    op = vie.Operator(n, 5e-3, 298e6, 1e-6)
+    op = vie.Operator(n, 5e-3, 298e6, 1e-6, rebuild="tcgen05")
     assert op.info()["rebuild_kernel"] == "tcgen05"
     J = dev(field(n, 2, 40))
     before = op.matvec(J)
