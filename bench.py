@@ -450,12 +450,16 @@ def run_headline(args):
     einc_h = einc.cpu().pin_memory()
     w_h = torch.empty_like(einc_h).pin_memory()
     k_e2e = min(args.steps, 3)
+    # device buffers the host data is copied into every step (allocated once:
+    # the same addresses let the solver replay its restart-cycle graphs)
+    c_d = torch.empty_like(chi_h, device="cuda")
+    e_d = torch.empty_like(einc_h, device="cuda")
     barrier()
     e2e_start = time.perf_counter()
     mv_e2e = 0
     for _ in range(k_e2e):
-        c_d = chi_h.to("cuda", non_blocking=True)
-        e_d = einc_h.to("cuda", non_blocking=True)
+        c_d.copy_(chi_h, non_blocking=True)
+        e_d.copy_(einc_h, non_blocking=True)
         _, inf = op.solve(c_d, e_d, out=w, **step_kw)
         mv_e2e += inf["matvecs"]
         w_h.copy_(w, non_blocking=True)
@@ -982,13 +986,16 @@ def run_solve64(args):
     kern_live = vie.profile_stop()
 
     # end to end: host buffers in, host solution out, through the same C-ABI solve
+    c_d = torch.empty_like(chi_h, device="cuda")
+    e_d = torch.empty_like(einc_h, device="cuda")
+    w_d = torch.empty_like(einc_h, device="cuda")
     barrier()
     e2e_start = time.perf_counter()
     mv_e2e = 0
     for _ in range(args.steps):
-        c_d = chi_h.to("cuda", non_blocking=True)
-        e_d = einc_h.to("cuda", non_blocking=True)
-        w, inf = op.solve(c_d, e_d, **solve_kw)
+        c_d.copy_(chi_h, non_blocking=True)
+        e_d.copy_(einc_h, non_blocking=True)
+        w, inf = op.solve(c_d, e_d, out=w_d, **solve_kw)
         mv_e2e += inf["matvecs"]
         w_h.copy_(w, non_blocking=True)
         torch.cuda.current_stream().synchronize()

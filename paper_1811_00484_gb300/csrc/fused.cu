@@ -662,13 +662,18 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
   constexpr bool kFs = (R == 2 || R == 4 || R == 6);
   const bool fs = kFs && (STORED || a.octant != nullptr);
   const size_t fs_smem = fused_fs_smem(4 * R, a.H3);
-  // P3 = 512: the three-pass radix-8 kernel (tp512.cu)
+  // P3 = 512: the three-pass radix-8 kernel (tp512.cu); P3 = 128: radix 8, 4, 4 (t128.cu)
   const bool tp = (R == 16) && fused_tp_supported(a, STORED);
+  const bool t128 = (R == 4) && fused_t128_supported(a, STORED);
   if (STORED || a.octant == nullptr) {
     ProfScope ps(fam, s);
     a.g0 = 0;
     if (tp) {
       launch_fused_tp(a, a.H1 * a.H2, STORED, s);
+      return;
+    }
+    if (t128) {
+      launch_fused_t128(a, a.H1 * a.H2, STORED, s);
       return;
     }
     if constexpr (kFs) {
@@ -694,8 +699,12 @@ static void launch_fused_warp_r(FusedArgs<float> a, cudaStream_t s) {
       launch_fused_tp(a, nk1 * a.H2, STORED, s);
       done = true;
     }
+    if (t128) {
+      launch_fused_t128(a, nk1 * a.H2, STORED, s);
+      done = true;
+    }
     if constexpr (kFs) {
-      if (fs) {
+      if (fs && !done) {
         launch_pdl(fused_fs_kernel<4 * R, STORED>, dim3(nk1 * a.H2), dim3(96), fs_smem, s, a);
         done = true;
       }

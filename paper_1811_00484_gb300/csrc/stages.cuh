@@ -727,5 +727,8 @@ bool launch_line_tp(LineArgs<float> a, cudaStream_t s);
 bool launch_line_tp64(LineArgs<double> a, cudaStream_t s);
 bool fused_tp_supported(const FusedArgs<float>& a, bool stored);
 void launch_fused_tp(const FusedArgs<float>& a, int groups, bool stored, cudaStream_t s);
+// P3 = 128 (64-voxel z edges): 16 threads per line, radix 8, 4, 4 (t128.cu)
+bool fused_t128_supported(const FusedArgs<float>& a, bool stored);
+void launch_fused_t128(const FusedArgs<float>& a, int groups, bool stored, cudaStream_t s);
 
 }  // namespace vie

@@ -32,10 +32,11 @@ HVOX = 5e-3
 K0 = K.wavenumber(F)
 
 GRIDS = [(3, 4, 5), (8, 8, 8), (6, 10, 20), (7, 5, 12), (16, 16, 16), (20, 9, 35)]
-# thin grids whose padded edges are 32 R for R = 2, 3, 5, 6, 8, 16: every radix of
-# the register-resident line and z-line FFTs, in both the x/y stages and z
+# thin grids whose padded edges are 32 R for R = 2, 3, 4, 5, 6, 8, 16: every radix of
+# the register-resident line and z-line FFTs, in both the x/y stages and z (n3 = 64:
+# the 16-thread-per-line z stage, with odd and even mirror-group counts)
 RADIX_GRIDS = [(48, 6, 32), (4, 80, 48), (6, 4, 80), (5, 6, 96), (4, 3, 128), (3, 4, 256),
-               (32, 3, 4)]
+               (5, 7, 64), (16, 12, 64), (32, 3, 4)]
 
 
 def dev(a, dtype=torch.complex64):
