@@ -640,83 +640,83 @@ __device__ __forceinline__ void fused_fs_group(const FusedArgs<float>& a, int g,
     C* line = a.data + (long long)(b * 3 + (act ? comp : 0)) * a.comp_stride + line_off;
     C v[V];
     if (act) {
-    // forward pass 1: x[j + 8 m], m < V/2 (the rest is zero padding)
+      // forward pass 1: x[j + 8 m], m < V/2 (the rest is zero padding)
 #pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int p = j + 8 * m;
-      v[m] = (m < V / 2 && valid && p < n3) ? line[p] : make_float2(0.f, 0.f);
-    }
-    reg_dft<C, float, V>(v, a.roots, N, false);
+      for (int m = 0; m < V; ++m) {
+        const int p = j + 8 * m;
+        v[m] = (m < V / 2 && valid && p < n3) ? line[p] : make_float2(0.f, 0.f);
+      }
+      reg_dft<C, float, V>(v, a.roots, N, false);
 #pragma unroll
-    for (int q = 1; q < V; ++q) v[q] = v[q] * a.roots[j * q];
+      for (int q = 1; q < V; ++q) v[q] = v[q] * a.roots[j * q];
 #pragma unroll
-    for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
-    __syncwarp();
-    // forward pass 2 -> spec[comp][ln][q + V k2]
-    C* sp = spec + (comp * 4 + ln) * SS;
+      for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
+      __syncwarp();
+      // forward pass 2 -> spec[comp][ln][q + V k2]
+      C* sp = spec + (comp * 4 + ln) * SS;
 #pragma unroll
-    for (int t = 0; t < V / 8; ++t) {
-      const int q = j + 8 * t;
-      C u[8];
+      for (int t = 0; t < V / 8; ++t) {
+        const int q = j + 8 * t;
+        C u[8];
 #pragma unroll
-      for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
-      reg_dft<C, float, 8>(u, a.roots, N, false);
+        for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
+        reg_dft<C, float, 8>(u, a.roots, N, false);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sp[q + V * k] = u[k];
-    }
+        for (int k = 0; k < 8; ++k) sp[q + V * k] = u[k];
+      }
     }
     __syncthreads();
     if (act) {
-    // product at f = j + 8 m, straight into the inverse pass 1 registers
-    const C* s0 = spec + (0 * 4 + ln) * SS;
-    const C* s1 = spec + (1 * 4 + ln) * SS;
-    const C* s2 = spec + (2 * 4 + ln) * SS;
+      // product at f = j + 8 m, straight into the inverse pass 1 registers
+      const C* s0 = spec + (0 * 4 + ln) * SS;
+      const C* s1 = spec + (1 * 4 + ln) * SS;
+      const C* s2 = spec + (2 * 4 + ln) * SS;
 #pragma unroll
-    for (int m = 0; m < V; ++m) {
-      const int f = j + 8 * m;
-      C G0, G1, G2;
-      float sz = 1.f;
-      if (STORED) {
-        const long long off = ((long long)kx * a.P2 + ky) * N + f;
-        G0 = a.spec[g0 * a.spec_stride + off];
-        G1 = a.spec[g1 * a.spec_stride + off];
-        G2 = a.spec[g2 * a.spec_stride + off];
-      } else {
-        const bool zm = 2 * f > N;
-        const int fold = zm ? N - f : f;
-        sz = zm ? -1.f : 1.f;
-        const C* gp = ghalf + ghalf_slot(fold);
-        G0 = gp[g0 * GS];
-        G1 = gp[g1 * GS];
-        G2 = gp[g2 * GS];
+      for (int m = 0; m < V; ++m) {
+        const int f = j + 8 * m;
+        C G0, G1, G2;
+        float sz = 1.f;
+        if (STORED) {
+          const long long off = ((long long)kx * a.P2 + ky) * N + f;
+          G0 = a.spec[g0 * a.spec_stride + off];
+          G1 = a.spec[g1 * a.spec_stride + off];
+          G2 = a.spec[g2 * a.spec_stride + off];
+        } else {
+          const bool zm = 2 * f > N;
+          const int fold = zm ? N - f : f;
+          sz = zm ? -1.f : 1.f;
+          const C* gp = ghalf + ghalf_slot(fold);
+          G0 = gp[g0 * GS];
+          G1 = gp[g1 * GS];
+          G2 = gp[g2 * GS];
+        }
+        // stored spectra are complete: no mirror signs
+        const float ex = STORED ? 1.f : sx, ey = STORED ? 1.f : sy;
+        C y = G0 * (ex * s0[f]) + G1 * (ey * s1[f]) + G2 * (sz * s2[f]);
+        if (!STORED) y = (comp == 2 ? sz : sc) * y;
+        v[m] = y;
       }
-      // stored spectra are complete: no mirror signs
-      const float ex = STORED ? 1.f : sx, ey = STORED ? 1.f : sy;
-      C y = G0 * (ex * s0[f]) + G1 * (ey * s1[f]) + G2 * (sz * s2[f]);
-      if (!STORED) y = (comp == 2 ? sz : sc) * y;
-      v[m] = y;
-    }
-    // inverse pass 1 (exchange buffer free: pass 2 read it before the barrier)
-    reg_dft<C, float, V>(v, a.roots, N, true);
+      // inverse pass 1 (exchange buffer free: pass 2 read it before the barrier)
+      reg_dft<C, float, V>(v, a.roots, N, true);
 #pragma unroll
-    for (int q = 1; q < V; ++q) v[q] = v[q] * conjg(a.roots[j * q]);
+      for (int q = 1; q < V; ++q) v[q] = v[q] * conjg(a.roots[j * q]);
 #pragma unroll
-    for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
-    __syncwarp();
-    // inverse pass 2, cropped: n = q + V k2 < N / 2
+      for (int q = 0; q < V; ++q) xc[j * (V + 1) + q] = v[q];
+      __syncwarp();
+      // inverse pass 2, cropped: n = q + V k2 < N / 2
 #pragma unroll
-    for (int t = 0; t < V / 8; ++t) {
-      const int q = j + 8 * t;
-      C u[8];
+      for (int t = 0; t < V / 8; ++t) {
+        const int q = j + 8 * t;
+        C u[8];
 #pragma unroll
-      for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
-      reg_dft<C, float, 8>(u, a.roots, N, true);
+        for (int l = 0; l < 8; ++l) u[l] = xc[l * (V + 1) + q];
+        reg_dft<C, float, 8>(u, a.roots, N, true);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int n = q + V * k;
-        if (valid && n < n3) line[n] = u[k];
+        for (int k = 0; k < 4; ++k) {
+          const int n = q + V * k;
+          if (valid && n < n3) line[n] = u[k];
+        }
       }
-    }
     }
     __syncthreads();                           // spec and xw reused by the next right-hand side
   }
