@@ -97,8 +97,8 @@ def test_multi_falls_back_for_other_edge_lengths():
 @pytest.mark.parametrize("n", [(32, 32, 32), (16, 24, 256)])
 def test_autotune_keeps_results(n):
     """The autotuner's choices (line-stage CTA sizes; the tcgen05 rebuild's k3
-    columns per CTA and CTAs per component, two range counts to choose from
-    at P3 = 512) change the speed only: the FP32 matvec agrees before and
+    columns per CTA and CTAs per component, several range counts to choose
+    from at P3 = 512) change the speed only: the FP32 matvec agrees before and
     after to FP32 rounding."""
     op = vie.Operator(n, 5e-3, 298e6, 1e-6, rebuild="tcgen05")
     assert op.info()["rebuild_kernel"] == "tcgen05"
